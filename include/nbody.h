@@ -1,0 +1,243 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) direct-summation N-body library.
+ *
+ * The library evaluates the all-pairs softened Newtonian acceleration and
+ * potential (Eq. 1 of Sec. 2.1, divided by m_i; softening "included in the
+ * distance computation" as in App. A, taken here as r^2 + eps^2), advances
+ * particles with kick-drift-kick leapfrog, and differentiates both.
+ *
+ *   a_i   =  G sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2}
+ *   phi_i = -G sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^{1/2}
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory:   every array argument is a DEVICE pointer owned by the caller,
+ *           8-byte aligned (256-byte for the workspace), C-contiguous.  The
+ *           library never allocates or frees device memory; scratch space is
+ *           the caller's workspace `ws` of `ws_bytes` bytes, sized with
+ *           nb_workspace_bytes() and ZERO-FILLED once before its first use
+ *           (the kernels leave their arrival counters at zero on exit, so
+ *           later calls need no clearing unless a call reported
+ *           NB_ERR_TIMEOUT).  One workspace serves one stream at a time.
+ * Layout:   positions, velocities, accelerations and their cotangents are
+ *           double [N][3] row-major; masses, potentials and their cotangents
+ *           double [N].  Batched sets concatenate clusters and describe them
+ *           with CSR offsets int64 [B+1] (offsets[0] = 0, offsets[B] = N).
+ * Streams:  all work is enqueued asynchronously on opts->stream (a
+ *           cudaStream_t; NULL = the legacy default stream).  Calls return
+ *           after enqueueing.
+ * Errors:   a call returns NB_OK or an NB_ERR_* code.  Argument errors are
+ *           detected on the host before anything is enqueued.  Errors found
+ *           on the device (a bounded wait that ran out, a non-finite result)
+ *           are latched in a status word inside `ws`; nb_poll_status() reads
+ *           and clears it.  nb_last_error() gives a message for the last
+ *           failing call on the calling host thread.
+ * Precision: inputs and outputs are always double.  opts->precision picks
+ *           the arithmetic of the pair loop: FP32 pairs with FP32, Kahan-
+ *           compensated FP32 or FP64 per-particle accumulation, or FP64
+ *           pairs.  The paper's device arithmetic is FP32 with the host in
+ *           FP64 (Sec. 3.1); the O(N) state updates here are FP64 on the GPU.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define NB_OK              0
+#define NB_ERR_INVALID     1  /* bad argument (size, pointer, alignment, value) */
+#define NB_ERR_CUDA        2  /* a CUDA runtime call failed                     */
+#define NB_ERR_WORKSPACE   3  /* ws_bytes smaller than nb_workspace_bytes()     */
+#define NB_ERR_UNSUPPORTED 4  /* valid request this build cannot serve          */
+#define NB_ERR_TIMEOUT     5  /* a device wait exceeded opts->timeout_cycles    */
+#define NB_ERR_NONFINITE   6  /* a non-finite value was produced                */
+
+/* ---- pair-loop precision policies ------------------------------------ */
+typedef enum {
+    NB_PREC_FP32 = 0,   /* FP32 pairs, FP32 running sums                      */
+    NB_PREC_KAHAN = 1,  /* FP32 pairs, per-tile FP32 sums Kahan-added         */
+    NB_PREC_F64ACC = 2, /* FP32 pairs, per-tile FP32 sums added in FP64       */
+    NB_PREC_FP64 = 3    /* FP64 pairs and sums                                */
+} nb_precision;
+
+/* Launch shape of the FP32-pair kernels.  Zero fields take the built-in
+ * defaults for the problem size; nb_tune_valid() reports whether a shape
+ * is one this build was compiled for. */
+typedef struct nb_tune {
+    int32_t threads;      /* threads per CTA: 128 or 256                   */
+    int32_t i_per_thread; /* i-particles held in registers per thread: 1,2,4,8 */
+    int32_t tile_j;       /* j-particles per shared-memory stage: 64..512   */
+    int32_t stages;       /* depth of the bulk-copy ring: 2..4               */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..4                    */
+} nb_tune;
+
+typedef struct nb_opts {
+    int32_t precision;      /* nb_precision                                   */
+    double G;               /* gravitational constant (units: G = 1 usual)    */
+    void *stream;           /* cudaStream_t or NULL                            */
+    int32_t use_graph;      /* nb_step: replay the step loop as a CUDA graph  */
+    const nb_tune *tune;    /* NULL = defaults                                 */
+    int64_t timeout_cycles; /* bound on every device wait, in SM clock cycles;
+                               0 = default (about 2 s)                         */
+} nb_opts;
+
+/* Fills *opts with precision F64ACC, G = 1, default stream, no graph,
+ * default tune and timeout. */
+void nb_opts_default(nb_opts *opts);
+
+/* Library version string and the list of compiled kernel shapes. */
+const char *nb_version(void);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char *nb_last_error(void);
+
+/* 1 if `tune` names a kernel shape compiled into this build, else 0. */
+int nb_tune_valid(const nb_tune *tune);
+
+/*
+ * Workspace bytes needed for problems of up to N_total particles in B
+ * clusters (B = 1 for a single system) under `opts` (precision and tune
+ * change the size).  Never fails; returns 0 for N_total < 1 or B < 1.
+ */
+size_t nb_workspace_bytes(int64_t N_total, int32_t B, const nb_opts *opts);
+
+/*
+ * Accelerations and potentials of one system (Eq. 1, Sec. 2.1; the pair
+ * kernel of App. A, Algorithm 3, without its jerk terms).
+ *   pos  [N][3], mass [N]         inputs
+ *   eps  >= 0                     Plummer softening length; eps == 0 selects
+ *                                 the guarded kernel that skips coincident
+ *                                 pairs (meant for tests and exact orbits)
+ *   acc  [N][3]                   output, overwritten
+ *   pot  [N] or NULL              output, overwritten when non-NULL
+ * Returns NB_ERR_INVALID for N < 1, NULL or misaligned arrays, eps < 0 or
+ * non-finite, or opts->G non-finite; NB_ERR_WORKSPACE if ws is too small.
+ */
+int nb_forces(const double *pos, const double *mass, int64_t N, double eps, double *acc,
+              double *pot, void *ws, size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * Accelerations and potentials of B independent clusters in one launch; the
+ * particles of cluster c are offsets[c] .. offsets[c+1]-1 and interact only
+ * with each other.  offsets (int64 [B+1]) and eps (double [B]) are device
+ * arrays; each cluster must hold between 1 and 8192 particles, and every
+ * eps[c] must be > 0.  Other arguments as nb_forces.  The work division over
+ * clusters follows the SPMD split of Sec. 3.1 (independent work per core).
+ */
+int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
+                      const double *eps, double *acc, double *pot, void *ws, size_t ws_bytes,
+                      const nb_opts *opts);
+
+/*
+ * State advanced by nb_step.  Single system: B = 1, offsets = NULL, eps used.
+ * Batched: B > 1 (or offsets != NULL), offsets/eps_b device arrays as in
+ * nb_forces_batched, eps ignored.  pos/vel/acc/pot device [N][3]/[N]
+ * (pot may be NULL).  acc_valid = 1 means acc already holds a(pos) (first-
+ * same-as-last reuse); nb_step sets it to 1 and adds nsteps to `step`.
+ */
+typedef struct nb_state {
+    int64_t N;
+    int32_t B;
+    const int64_t *offsets;
+    double *pos;
+    double *vel;
+    const double *mass;
+    double *acc;
+    double *pot;
+    const double *eps_b;
+    double eps;
+    int64_t step;
+    int32_t acc_valid;
+    void *ws;
+    size_t ws_bytes;
+} nb_state;
+
+/*
+ * nsteps kick-drift-kick leapfrog steps of size dt:
+ *   v += (dt/2) a(x);  x += dt v;  v += (dt/2) a(x)
+ * The paper advances with a predict-evaluate-correct Hermite scheme (Sec. 2.1)
+ * around the same all-pairs evaluation; this library uses leapfrog.  The
+ * batched form runs every step of all clusters inside one persistent launch.
+ * dt must be finite, nsteps >= 0.
+ */
+int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *opts);
+
+/*
+ * Energy bookkeeping of the state: out3 (device double[3]) receives
+ * K = 1/2 sum m |v|^2, W = 1/2 sum m phi, E = K + W, summed in a fixed order
+ * (bitwise reproducible).  Needs s->pot valid (call after nb_forces or
+ * nb_step with a non-NULL pot).  For batched states the sums run over all
+ * clusters together.
+ */
+int nb_energy(const nb_state *s, double *out3, const nb_opts *opts);
+
+/*
+ * Vector-Jacobian product of (a, phi) with respect to (x, m) at (pos, mass):
+ *   pos_bar_k  = sum_i (d a_i/d x_k)^T acc_bar_i + sum_i (d phi_i/d x_k) pot_bar_i
+ *   mass_bar_k = sum_i (d a_i/d m_k) . acc_bar_i + sum_i (d phi_i/d m_k) pot_bar_i
+ * i.e. pos_bar_k = G sum_{j!=k} K(d)(m_k abar_j - m_j abar_k)
+ *                  - G sum_{j!=k} s^-3 (m_k pbar_j + m_j pbar_k) d,
+ *      mass_bar_k = -G sum_{j!=k} (s^-3 abar_j . d + s^-1 pbar_j),
+ * with d = x_j - x_k, s^2 = |d|^2 + eps^2, K(d) = s^-3 I - 3 s^-5 d d^T.
+ * acc_bar [N][3] in; pot_bar [N] in or NULL (zero); pos_bar [N][3] and
+ * mass_bar [N] out, overwritten.  Derived from Eq. 1; the paper itself does
+ * not differentiate its simulation.
+ */
+int nb_forces_vjp(const double *pos, const double *mass, int64_t N, double eps,
+                  const double *acc_bar, const double *pot_bar, double *pos_bar,
+                  double *mass_bar, void *ws, size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * One merged reverse step of the discrete KDK adjoint at positions pos_k:
+ *   vel_bar  += drift_dt * pos_bar          (adjoint of the drift x += dt v)
+ *   c         = kick_coef * vel_bar          (cotangent of the kicks at x_k)
+ *   pos_bar  += J_x(pos_k)^T c,  mass_bar += J_m(pos_k)^T c
+ * where J is the Jacobian of a(x, m).  The reverse sweep of K steps of size
+ * h from the final cotangents is: one call at x_K with (drift_dt, kick_coef)
+ * = (0, h/2); calls at x_{K-1} .. x_1 with (h, h); one call at x_0 with
+ * (h, h/2).  The two half-kick cotangents meeting at each interior x_k are
+ * thereby applied in one VJP.  pos_bar, vel_bar, mass_bar are read and
+ * updated in place.
+ */
+int nb_step_vjp(const double *pos_k, const double *mass, int64_t N, double eps, double drift_dt,
+                double kick_coef, double *pos_bar, double *vel_bar, double *mass_bar, void *ws,
+                size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * Reverse-time reconstruction fused with the adjoint: one call replaces a
+ * recomputed forward step plus nb_step_vjp when the trajectory is rebuilt
+ * backwards instead of stored.  With the positions x_k in pos:
+ *   acc      = a(x_k)                       (written)
+ *   vel_bar, pos_bar, mass_bar              updated exactly as
+ *                                           nb_step_vjp(x_k, drift_dt, kick_coef)
+ *   vhalf   -= rewind_kick * acc;  pos -= rewind_drift * vhalf
+ * With vhalf = v_{k+1/2} and rewind_kick = rewind_drift = h this leaves
+ * v_{k-1/2} and x_{k-1}; with vhalf = v_k and rewind_kick = h/2 it starts
+ * the rewind from a stored full-step state; zeros leave the state alone.
+ * The leapfrog map is time-reversible, so this recovers the forward
+ * trajectory up to rounding; callers re-anchor at stored checkpoints.
+ * pos, vhalf, acc: device [N][3]; the pair loop reads a packed copy of pos
+ * taken before any update.
+ */
+int nb_step_vjp_reverse(double *pos, double *vhalf, double *acc, const double *mass, int64_t N,
+                        double eps, double rewind_kick, double rewind_drift, double drift_dt,
+                        double kick_coef, double *pos_bar, double *vel_bar, double *mass_bar,
+                        void *ws, size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * Synchronises `stream`, reads the device status word latched in ws (a
+ * bitwise OR of 1 << NB_ERR_TIMEOUT and 1 << NB_ERR_NONFINITE), clears it,
+ * and returns the matching NB_ERR_* code (timeout first) or NB_OK.
+ */
+int nb_poll_status(void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

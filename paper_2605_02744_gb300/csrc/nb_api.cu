@@ -1,0 +1,531 @@
+// Host side of the C ABI (include/nbody.h): argument checks, workspace
+// layout, launch-shape choice, the leapfrog driver and CUDA-graph replay.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "nb_internal.h"
+
+namespace nb {
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+int cuda_check(cudaError_t e, const char *what) {
+    return fail(NB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------- device
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();  // no device here: size for a full GB300
+        return 152;
+    }
+    return n;
+}
+
+// ------------------------------------------------------------ shapes
+bool force_shape_compiled(const Shape &s);
+bool vjp_shape_compiled(const Shape &s);
+
+bool shape_compiled(const Shape &s, int kind) {
+    return kind == kKindForce ? force_shape_compiled(s) : vjp_shape_compiled(s);
+}
+
+Shape default_shape(int64_t N, int precision, int kind) {
+    (void)precision;
+    if (kind == kKindForce) {
+        if (N >= (1 << 17)) return Shape{256, 4, 256, 3, 2};
+        if (N >= (1 << 13)) return Shape{128, 2, 128, 3, 4};
+        return Shape{128, 1, 64, 2, 4};
+    }
+    if (N >= (1 << 15)) return Shape{128, 2, 128, 3, 4};
+    return Shape{128, 1, 64, 2, 4};
+}
+
+bool resolve_shape(const nb_opts *opts, int64_t N, int kind, Shape *out) {
+    Shape s = default_shape(N, opts ? opts->precision : NB_PREC_F64ACC, kind);
+    if (opts && opts->tune) {
+        const nb_tune *t = opts->tune;
+        if (t->threads) s.threads = t->threads;
+        if (t->i_per_thread) s.ipt = t->i_per_thread;
+        if (t->tile_j) s.tile_j = t->tile_j;
+        if (t->stages) s.stages = t->stages;
+        if (t->ctas_per_sm) s.ctas_per_sm = t->ctas_per_sm;
+    }
+    if (s.ctas_per_sm < 1 || s.ctas_per_sm > 4) return false;
+    *out = s;
+    return shape_compiled(s, kind);
+}
+
+// ---------------------------------------------------------- workspace
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int64_t kPadParticles = 2048;  // >= every i-block and j-tile size
+constexpr int64_t kForceRecordBytes = 32;
+constexpr int64_t kVjpRecordBytes = 128;
+constexpr size_t kScratchBase = 64 * 1024;
+
+WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
+    WsLayout L{};
+    if (N < 1) N = 1;
+    if (B < 1) B = 1;
+    Shape sf, sv;
+    if (!resolve_shape(opts, N, kKindForce, &sf)) sf = default_shape(N, 0, kKindForce);
+    if (!resolve_shape(opts, N, kKindVjp, &sv)) sv = default_shape(N, 0, kKindVjp);
+    L.Np = round_up(N, kPadParticles);
+    const int64_t sms = device_sm_count();
+    L.max_grid = 4 * sms;
+    L.max_blocks = cdiv(N, 64) + 1;
+    L.record_bytes_per_i = std::max(kForceRecordBytes * sf.block_i(),
+                                    kVjpRecordBytes * sv.block_i());
+    size_t off = 0;
+    L.status = off;
+    off = align256(off + 256);
+    L.counters = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)L.max_blocks);
+    L.packA = off;
+    off = align256(off + 16 * (size_t)L.Np);
+    L.packB = off;
+    off = align256(off + 16 * (size_t)L.Np);
+    L.records = off;
+    off = align256(off + 2 * (size_t)L.max_grid * (size_t)L.record_bytes_per_i);
+    L.scratch = off;
+    off = align256(off + kScratchBase + batched_scratch_bytes(B));
+    L.total = off;
+    return L;
+}
+
+int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L) {
+    if (!ws) return fail(NB_ERR_INVALID, "workspace pointer is NULL");
+    if (((uintptr_t)ws & 255) != 0) return fail(NB_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(NB_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes,
+                    L.total);
+    return NB_OK;
+}
+
+// ------------------------------------------------------------ checks
+static int check_ptr(const void *p, const char *name, bool nullable = false) {
+    if (!p) return nullable ? NB_OK : fail(NB_ERR_INVALID, "%s is NULL", name);
+    if (((uintptr_t)p & 7) != 0) return fail(NB_ERR_INVALID, "%s is not 8-byte aligned", name);
+    return NB_OK;
+}
+
+static int check_common(const nb_opts *o, int64_t N, double eps) {
+    if (!o) return fail(NB_ERR_INVALID, "opts is NULL");
+    if (N < 1) return fail(NB_ERR_INVALID, "N must be >= 1 (got %lld)", (long long)N);
+    if (N > (int64_t)1 << 30) return fail(NB_ERR_INVALID, "N above 2^30 is not supported");
+    if (!(eps >= 0.0) || !isfinite(eps)) return fail(NB_ERR_INVALID, "eps must be finite and >= 0");
+    if (eps > 0.0 && (float)eps * (float)eps < 1.2e-38f)
+        return fail(NB_ERR_INVALID, "eps^2 underflows FP32; use eps = 0 or eps >= 1.1e-19");
+    if (!isfinite(o->G)) return fail(NB_ERR_INVALID, "G must be finite");
+    if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
+        return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
+    if (o->timeout_cycles < 0) return fail(NB_ERR_INVALID, "timeout_cycles must be >= 0");
+    return NB_OK;
+}
+
+static long long timeout_of(const nb_opts *o) {
+    return o->timeout_cycles > 0 ? (long long)o->timeout_cycles : kDefaultTimeoutCycles;
+}
+
+#define NB_TRY(expr)              \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != NB_OK) return rc_; \
+    } while (0)
+
+static int make_force_job(ForceJob *j, const double *pos, const double *mass, int64_t N,
+                          double eps, double *acc, double *pot, void *ws, size_t ws_bytes,
+                          const nb_opts *o) {
+    NB_TRY(check_common(o, N, eps));
+    NB_TRY(check_ptr(pos, "pos"));
+    NB_TRY(check_ptr(mass, "mass"));
+    NB_TRY(check_ptr(acc, "acc"));
+    NB_TRY(check_ptr(pot, "pot", true));
+    j->L = ws_layout(N, 1, o);
+    NB_TRY(check_ws(ws, ws_bytes, j->L));
+    if (o->precision != NB_PREC_FP64 && !resolve_shape(o, N, kKindForce, &j->shape))
+        return fail(NB_ERR_UNSUPPORTED, "requested force kernel shape is not compiled");
+    j->pos = pos;
+    j->mass = mass;
+    j->N = N;
+    j->eps = eps;
+    j->G = o->G;
+    j->acc = acc;
+    j->pot = pot;
+    j->vel = nullptr;
+    j->kick = 0.0;
+    j->precision = o->precision;
+    j->packed_ready = false;
+    j->timeout = timeout_of(o);
+    j->stream = (cudaStream_t)o->stream;
+    j->ws = (char *)ws;
+    return NB_OK;
+}
+
+// ------------------------------------------------------- graph cache
+struct GraphKey {
+    nb_state s;
+    double dt;
+    int64_t nsteps;
+    nb_opts o;
+    nb_tune t;
+    int device;
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxGraphs = 16;
+
+static bool same_key(const GraphKey &a, const GraphKey &b) {
+    return memcmp(&a, &b, sizeof(GraphKey)) == 0;
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+// =================================================================== ABI
+extern "C" {
+
+void nb_opts_default(nb_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = NB_PREC_F64ACC;
+    o->G = 1.0;
+}
+
+const char *nb_version(void) {
+    return "nbody-gb300 1.0 (sm_103a; FP32 pairs with FP32/Kahan/FP64 accumulation, FP64 pairs)";
+}
+
+const char *nb_last_error(void) { return g_err; }
+
+int nb_tune_valid(const nb_tune *t) {
+    if (!t) return 0;
+    nb_opts o;
+    nb_opts_default(&o);
+    o.tune = t;
+    Shape s;
+    return resolve_shape(&o, 1 << 20, kKindForce, &s) ? 1 : 0;
+}
+
+size_t nb_workspace_bytes(int64_t N_total, int32_t B, const nb_opts *opts) {
+    if (N_total < 1 || B < 1) return 0;
+    return ws_layout(N_total, B, opts).total;
+}
+
+int nb_forces(const double *pos, const double *mass, int64_t N, double eps, double *acc,
+              double *pot, void *ws, size_t ws_bytes, const nb_opts *opts) {
+    clear_error();
+    ForceJob j;
+    NB_TRY(make_force_job(&j, pos, mass, N, eps, acc, pot, ws, ws_bytes, opts));
+    return launch_force(j);
+}
+
+int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
+                      const double *eps, double *acc, double *pot, void *ws, size_t ws_bytes,
+                      const nb_opts *o) {
+    clear_error();
+    if (!o) return fail(NB_ERR_INVALID, "opts is NULL");
+    if (B < 1) return fail(NB_ERR_INVALID, "B must be >= 1");
+    NB_TRY(check_ptr(pos, "pos"));
+    NB_TRY(check_ptr(mass, "mass"));
+    NB_TRY(check_ptr(offsets, "offsets"));
+    NB_TRY(check_ptr(eps, "eps"));
+    NB_TRY(check_ptr(acc, "acc"));
+    NB_TRY(check_ptr(pot, "pot", true));
+    if (!isfinite(o->G)) return fail(NB_ERR_INVALID, "G must be finite");
+    if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
+        return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
+    // N_total is only known on the device; the caller's workspace must have
+    // been sized with the same B and an N_total that bounds offsets[B].
+    BatchedJob j{};
+    j.L = ws_layout(1, B, o);
+    if (!ws || ((uintptr_t)ws & 255)) return fail(NB_ERR_INVALID, "workspace NULL or misaligned");
+    if (ws_bytes < j.L.total) return fail(NB_ERR_WORKSPACE, "workspace too small for B=%d", B);
+    j.mass = mass;
+    j.offsets = offsets;
+    j.B = B;
+    j.eps = eps;
+    j.G = o->G;
+    j.pos = const_cast<double *>(pos);
+    j.vel = nullptr;
+    j.acc = acc;
+    j.pot = pot;
+    j.N = -1;
+    j.dt = 0.0;
+    j.nsteps = 0;
+    j.acc_valid = false;
+    j.precision = o->precision;
+    j.timeout = timeout_of(o);
+    j.stream = (cudaStream_t)o->stream;
+    j.ws = (char *)ws;
+    return launch_batched(j);
+}
+
+static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
+    ForceJob j;
+    NB_TRY(make_force_job(&j, s->pos, s->mass, s->N, s->eps, s->acc, s->pot, s->ws, s->ws_bytes, o));
+    if (!s->acc_valid) NB_TRY(launch_force(j));
+    float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        NB_TRY(launch_kick_drift_pack(s->pos, s->vel, s->acc, s->mass, s->N, j.L.Np, dt, soa,
+                                      j.stream));
+        ForceJob k = j;
+        k.packed_ready = true;
+        k.vel = s->vel;
+        k.kick = 0.5 * dt;
+        NB_TRY(launch_force(k));
+    }
+    return NB_OK;
+}
+
+int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
+    clear_error();
+    if (!s) return fail(NB_ERR_INVALID, "state is NULL");
+    if (!o) return fail(NB_ERR_INVALID, "opts is NULL");
+    if (!isfinite(dt)) return fail(NB_ERR_INVALID, "dt must be finite");
+    if (nsteps < 0) return fail(NB_ERR_INVALID, "nsteps must be >= 0");
+    NB_TRY(check_ptr(s->pos, "state.pos"));
+    NB_TRY(check_ptr(s->vel, "state.vel"));
+    NB_TRY(check_ptr(s->mass, "state.mass"));
+    NB_TRY(check_ptr(s->acc, "state.acc"));
+    NB_TRY(check_ptr(s->pot, "state.pot", true));
+    if (s->B > 1 || s->offsets) {
+        if (s->B < 1) return fail(NB_ERR_INVALID, "B must be >= 1");
+        NB_TRY(check_ptr(s->offsets, "state.offsets"));
+        NB_TRY(check_ptr(s->eps_b, "state.eps_b"));
+        if (s->N < 1) return fail(NB_ERR_INVALID, "N must be >= 1");
+        BatchedJob j{};
+        j.L = ws_layout(s->N, s->B, o);
+        NB_TRY(check_ws(s->ws, s->ws_bytes, j.L));
+        j.mass = s->mass;
+        j.offsets = s->offsets;
+        j.B = s->B;
+        j.eps = s->eps_b;
+        j.G = o->G;
+        j.pos = s->pos;
+        j.vel = s->vel;
+        j.acc = s->acc;
+        j.pot = s->pot;
+        j.N = s->N;
+        j.dt = dt;
+        j.nsteps = nsteps;
+        j.acc_valid = s->acc_valid != 0;
+        j.precision = o->precision;
+        j.timeout = timeout_of(o);
+        j.stream = (cudaStream_t)o->stream;
+        j.ws = (char *)s->ws;
+        NB_TRY(launch_batched(j));
+        s->acc_valid = 1;
+        s->step += nsteps;
+        return NB_OK;
+    }
+    NB_TRY(check_common(o, s->N, s->eps));
+    const bool graph = o->use_graph && o->stream != nullptr && nsteps > 0;
+    if (!graph) {
+        NB_TRY(step_single_direct(s, dt, nsteps, o));
+    } else {
+        GraphKey key;
+        memset(&key, 0, sizeof key);
+        key.s.N = s->N;
+        key.s.B = s->B;
+        key.s.offsets = s->offsets;
+        key.s.pos = s->pos;
+        key.s.vel = s->vel;
+        key.s.mass = s->mass;
+        key.s.acc = s->acc;
+        key.s.pot = s->pot;
+        key.s.eps_b = s->eps_b;
+        key.s.eps = s->eps;
+        key.s.acc_valid = s->acc_valid;
+        key.s.ws = s->ws;
+        key.s.ws_bytes = s->ws_bytes;
+        key.dt = dt;
+        key.nsteps = nsteps;
+        key.o.precision = o->precision;
+        key.o.G = o->G;
+        key.o.stream = o->stream;
+        key.o.use_graph = o->use_graph;
+        key.o.timeout_cycles = o->timeout_cycles;
+        if (o->tune) {
+            key.t.threads = o->tune->threads;
+            key.t.i_per_thread = o->tune->i_per_thread;
+            key.t.tile_j = o->tune->tile_j;
+            key.t.stages = o->tune->stages;
+            key.t.ctas_per_sm = o->tune->ctas_per_sm;
+        }
+        cudaGetDevice(&key.device);
+        cudaGraphExec_t exec = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            for (auto &e : g_graphs)
+                if (same_key(e.key, key)) exec = e.exec;
+        }
+        cudaStream_t st = (cudaStream_t)o->stream;
+        if (!exec) {
+            // The first call of a new configuration captures the loop (state
+            // pointers, sizes and dt are baked into the graph).
+            NB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rc = step_single_direct(s, dt, nsteps, o);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc != NB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return cuda_check(ce, "cudaStreamEndCapture");
+            const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return cuda_check(ie, "cudaGraphInstantiate");
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            if (g_graphs.size() >= kMaxGraphs) {
+                cudaGraphExecDestroy(g_graphs.front().exec);
+                g_graphs.erase(g_graphs.begin());
+            }
+            // the captured graph includes the priming force only if acc was invalid
+            g_graphs.push_back(GraphEntry{key, exec});
+        }
+        NB_CUDA(cudaGraphLaunch(exec, st));
+    }
+    s->acc_valid = 1;
+    s->step += nsteps;
+    return NB_OK;
+}
+
+int nb_energy(const nb_state *s, double *out3, const nb_opts *o) {
+    clear_error();
+    if (!s || !o) return fail(NB_ERR_INVALID, "state or opts is NULL");
+    if (s->N < 1) return fail(NB_ERR_INVALID, "N must be >= 1");
+    NB_TRY(check_ptr(s->vel, "state.vel"));
+    NB_TRY(check_ptr(s->mass, "state.mass"));
+    NB_TRY(check_ptr(s->pot, "state.pot"));
+    NB_TRY(check_ptr(out3, "out3"));
+    WsLayout L = ws_layout(s->N, s->B < 1 ? 1 : s->B, o);
+    NB_TRY(check_ws(s->ws, s->ws_bytes, L));
+    return launch_energy(s->vel, s->mass, s->pot, s->N, out3, (char *)s->ws, L,
+                         (cudaStream_t)o->stream);
+}
+
+static int make_vjp_job(VjpJob *j, const double *pos, const double *mass, int64_t N, double eps,
+                        double *pos_bar, double *mass_bar, void *ws, size_t ws_bytes,
+                        const nb_opts *o) {
+    memset(j, 0, sizeof *j);
+    NB_TRY(check_common(o, N, eps));
+    NB_TRY(check_ptr(pos, "pos"));
+    NB_TRY(check_ptr(mass, "mass"));
+    NB_TRY(check_ptr(pos_bar, "pos_bar"));
+    NB_TRY(check_ptr(mass_bar, "mass_bar"));
+    j->L = ws_layout(N, 1, o);
+    NB_TRY(check_ws(ws, ws_bytes, j->L));
+    if (o->precision != NB_PREC_FP64 && !resolve_shape(o, N, kKindVjp, &j->shape))
+        return fail(NB_ERR_UNSUPPORTED, "requested VJP kernel shape is not compiled");
+    j->pos = pos;
+    j->mass = mass;
+    j->N = N;
+    j->eps = eps;
+    j->G = o->G;
+    j->pos_bar = pos_bar;
+    j->mass_bar = mass_bar;
+    j->precision = o->precision;
+    j->timeout = timeout_of(o);
+    j->stream = (cudaStream_t)o->stream;
+    j->ws = (char *)ws;
+    return NB_OK;
+}
+
+int nb_forces_vjp(const double *pos, const double *mass, int64_t N, double eps,
+                  const double *acc_bar, const double *pot_bar, double *pos_bar, double *mass_bar,
+                  void *ws, size_t ws_bytes, const nb_opts *o) {
+    clear_error();
+    VjpJob j;
+    NB_TRY(make_vjp_job(&j, pos, mass, N, eps, pos_bar, mass_bar, ws, ws_bytes, o));
+    NB_TRY(check_ptr(acc_bar, "acc_bar"));
+    NB_TRY(check_ptr(pot_bar, "pot_bar", true));
+    j.acc_bar = acc_bar;
+    j.pot_bar = pot_bar;
+    j.step_form = false;
+    j.accumulate = false;
+    return launch_vjp(j);
+}
+
+int nb_step_vjp(const double *pos_k, const double *mass, int64_t N, double eps, double drift_dt,
+                double kick_coef, double *pos_bar, double *vel_bar, double *mass_bar, void *ws,
+                size_t ws_bytes, const nb_opts *o) {
+    clear_error();
+    VjpJob j;
+    NB_TRY(make_vjp_job(&j, pos_k, mass, N, eps, pos_bar, mass_bar, ws, ws_bytes, o));
+    NB_TRY(check_ptr(vel_bar, "vel_bar"));
+    if (!isfinite(drift_dt) || !isfinite(kick_coef))
+        return fail(NB_ERR_INVALID, "drift_dt and kick_coef must be finite");
+    j.step_form = true;
+    j.drift_dt = drift_dt;
+    j.kick_coef = kick_coef;
+    j.vel_bar = vel_bar;
+    j.accumulate = true;
+    return launch_vjp(j);
+}
+
+int nb_step_vjp_reverse(double *pos, double *vhalf, double *acc, const double *mass, int64_t N,
+                        double eps, double rewind_kick, double rewind_drift, double drift_dt,
+                        double kick_coef, double *pos_bar, double *vel_bar, double *mass_bar,
+                        void *ws, size_t ws_bytes, const nb_opts *o) {
+    clear_error();
+    VjpJob j;
+    NB_TRY(make_vjp_job(&j, pos, mass, N, eps, pos_bar, mass_bar, ws, ws_bytes, o));
+    NB_TRY(check_ptr(vel_bar, "vel_bar"));
+    NB_TRY(check_ptr(vhalf, "vhalf"));
+    NB_TRY(check_ptr(acc, "acc"));
+    if (!isfinite(drift_dt) || !isfinite(kick_coef) || !isfinite(rewind_kick) ||
+        !isfinite(rewind_drift))
+        return fail(NB_ERR_INVALID, "step coefficients must be finite");
+    j.step_form = true;
+    j.drift_dt = drift_dt;
+    j.kick_coef = kick_coef;
+    j.vel_bar = vel_bar;
+    j.accumulate = true;
+    j.acc_out = acc;
+    j.vhalf = vhalf;
+    j.pos_rw = pos;
+    j.rewind_kick = rewind_kick;
+    j.rewind_drift = rewind_drift;
+    return launch_vjp(j);
+}
+
+int nb_poll_status(void *ws, size_t ws_bytes, void *stream) {
+    clear_error();
+    if (!ws || ws_bytes < 256) return fail(NB_ERR_INVALID, "workspace NULL or too small");
+    NB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t word = 0;
+    NB_CUDA(cudaMemcpy(&word, ws, sizeof word, cudaMemcpyDeviceToHost));
+    if (word) NB_CUDA(cudaMemset(ws, 0, sizeof word));
+    if (word & kStatusTimeout) return fail(NB_ERR_TIMEOUT, "a device wait ran out of time");
+    if (word & kStatusInvalid) return fail(NB_ERR_INVALID, "the device rejected an argument");
+    if (word & kStatusNonFinite) return fail(NB_ERR_NONFINITE, "a non-finite value was produced");
+    return NB_OK;
+}
+
+}  // extern "C"

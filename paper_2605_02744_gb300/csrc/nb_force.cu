@@ -1,0 +1,433 @@
+// All-pairs softened acceleration + potential (Eq. 1, Sec. 2.1; pair kernel of
+// App. A, Algorithm 3, without the jerk terms).
+//
+// FP32-pair kernel ("stream-K"): the iteration space is (i-block, j-tile)
+// pairs, i-block = NT*IR particles held in registers, j-tile = TJ particles
+// staged in shared memory.  The pairs are laid out i-block-major and cut into
+// equal contiguous ranges, one per persistent CTA, so every SM gets the same
+// number of pair interactions whatever N is.  A CTA whose range covers an
+// i-block only in part writes that block's partial sums to a record in the
+// workspace; the last CTA to arrive at a block (arrival counter) folds the
+// records in CTA order, so the result does not depend on timing.
+//
+// j-tiles are streamed through a ST-deep ring of shared-memory stages filled
+// by bulk asynchronous copies (cp.async.bulk, one per SoA component) that
+// complete on mbarriers -- the GB300 analogue of the read kernel feeding
+// circular buffers in Algorithm 1.  The pair loop processes two j-particles
+// per packed f32x2 instruction (13 packed FP32 operations and 2 MUFU rsqrt
+// per two pairs).
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nb {
+
+using dev::Acc;
+using dev::Record;
+
+// ------------------------------------------------------------------ pack
+// FP64 [N][3] positions + [N] masses -> float SoA x[Np] y[Np] z[Np] m[Np],
+// round-to-nearest; entries N..Np-1 are zero-mass particles at the origin.
+__global__ void pack_soa_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
+                                int64_t N, int64_t Np, float *__restrict__ soa) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float x = 0.f, y = 0.f, z = 0.f, m = 0.f;
+        if (i < N) {
+            x = __double2float_rn(pos[3 * i]);
+            y = __double2float_rn(pos[3 * i + 1]);
+            z = __double2float_rn(pos[3 * i + 2]);
+            m = __double2float_rn(mass[i]);
+        }
+        soa[i] = x;
+        soa[Np + i] = y;
+        soa[2 * Np + i] = z;
+        soa[3 * Np + i] = m;
+    }
+}
+
+int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
+                cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>(cdiv(Np, threads), 8192);
+    pack_soa_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, mass, N, Np, soa);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// ----------------------------------------------------------- FP32 pairs
+struct ForceParams {
+    const float *soa;  // [4][Np]
+    int64_t Np;
+    int64_t N;
+    int64_t total;  // nblocks * ntiles
+    int32_t nblocks;
+    int32_t ntiles;
+    float eps2;
+    double G;
+    double *acc;
+    double *pot;
+    double *vel;
+    double kick;
+    Record *records;
+    uint32_t *counters;
+    uint32_t *status;
+    long long timeout;
+};
+
+template <int IR, bool GUARD>
+__device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const float2 zj,
+                                      const float2 mj, const float2 eps2, const float2 (&nx)[IR],
+                                      const float2 (&ny)[IR], const float2 (&nz)[IR],
+                                      float2 (&ax)[IR], float2 (&ay)[IR], float2 (&az)[IR],
+                                      float2 (&ph)[IR]) {
+    using namespace dev;
+#pragma unroll
+    for (int k = 0; k < IR; ++k) {
+        const float2 dx = add2(xj, nx[k]);
+        const float2 dy = add2(yj, ny[k]);
+        const float2 dz = add2(zj, nz[k]);
+        float2 r2 = fma2(dx, dx, eps2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        if (GUARD) {
+            ri.x = r2.x > 0.f ? ri.x : 0.f;
+            ri.y = r2.y > 0.f ? ri.y : 0.f;
+        }
+        const float2 s = mul2(mj, ri);
+        const float2 ri2 = mul2(ri, ri);
+        const float2 s3 = mul2(s, ri2);
+        ax[k] = fma2(s3, dx, ax[k]);
+        ay[k] = fma2(s3, dy, ay[k]);
+        az[k] = fma2(s3, dz, az[k]);
+        ph[k] = add2(ph[k], s);
+    }
+}
+
+template <int NT, int IR, int POL, bool GUARD>
+__device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
+                                               const Acc<POL> (&acc)[IR][4], const float (&mi)[IR]) {
+    constexpr int BI = NT * IR;
+    uint32_t bad = 0;
+#pragma unroll
+    for (int k = 0; k < IR; ++k) {
+        const int64_t i = b * BI + k * NT + threadIdx.x;
+        if (i < p.N) {
+            double phs = acc[k][3].value();
+            if (!GUARD) phs -= (double)(mi[k] * dev::rsqrt_approx(p.eps2));  // self pair
+            const double gx = p.G * acc[k][0].value();
+            const double gy = p.G * acc[k][1].value();
+            const double gz = p.G * acc[k][2].value();
+            const double gp = -p.G * phs;
+            p.acc[3 * i] = gx;
+            p.acc[3 * i + 1] = gy;
+            p.acc[3 * i + 2] = gz;
+            if (p.pot) p.pot[i] = gp;
+            if (p.vel) {
+                p.vel[3 * i] += p.kick * gx;
+                p.vel[3 * i + 1] += p.kick * gy;
+                p.vel[3 * i + 2] += p.kick * gz;
+            }
+            if (!(isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(gp))) bad = 1;
+        }
+    }
+    if (bad) dev::set_status(p.status, kStatusNonFinite);
+}
+
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD>
+__global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
+    using namespace dev;
+    constexpr int BI = NT * IR;
+    static_assert(TJ % 4 == 0 && (TJ * 4) % 16 == 0, "tile must be 16-byte granular");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *stages = reinterpret_cast<float *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + ST * 16 * TJ);
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int64_t C = gridDim.x, c = blockIdx.x;
+    const int64_t L0 = sk_lo(p.total, C, c);
+    const int64_t nq = sk_lo(p.total, C, c + 1) - L0;
+    if (nq <= 0) return;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < ST; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t q) {
+        const int s = (int)(q % ST);
+        const int64_t jt = (L0 + q) % p.ntiles;
+        float *dst = stages + s * 4 * TJ;
+        mbar_arrive_expect_tx(&full[s], 16 * TJ);
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp)
+            bulk_g2s(dst + comp * TJ, p.soa + comp * p.Np + jt * TJ, 4 * TJ, &full[s]);
+    };
+    if (tid == 0) {
+        for (int64_t q = 0; q < nq && q < ST; ++q) issue(q);
+    }
+
+    float2 nx[IR], ny[IR], nz[IR];
+    float mi[IR];
+    Acc<POL> acc[IR][4];
+    const float2 eps2 = f2(p.eps2, p.eps2);
+    int64_t b = 0, seg_begin = 0;
+    const int64_t first_block = L0 / p.ntiles;
+
+    for (int64_t q = 0; q < nq; ++q) {
+        const int64_t t = L0 + q;
+        const int64_t jt = t % p.ntiles;
+        if (q == 0 || jt == 0) {
+            b = t / p.ntiles;
+            seg_begin = jt;
+#pragma unroll
+            for (int k = 0; k < IR; ++k) {
+                const int64_t i = b * BI + k * NT + tid;
+                const float x = p.soa[i], y = p.soa[p.Np + i], z = p.soa[2 * p.Np + i];
+                mi[k] = p.soa[3 * p.Np + i];
+                nx[k] = f2(-x, -x);
+                ny[k] = f2(-y, -y);
+                nz[k] = f2(-z, -z);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[k][e].zero();
+            }
+        }
+        const int s = (int)(q % ST);
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((q / ST) & 1), p.timeout);
+        const float *sx = stages + s * 4 * TJ;
+        const float *sy = sx + TJ;
+        const float *sz = sx + 2 * TJ;
+        const float *sm = sx + 3 * TJ;
+
+        float2 ax[IR], ay[IR], az[IR], ph[IR];
+#pragma unroll
+        for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
+#pragma unroll 2
+        for (int jj = 0; jj < TJ; jj += 4) {
+            const float4 X = *reinterpret_cast<const float4 *>(sx + jj);
+            const float4 Y = *reinterpret_cast<const float4 *>(sy + jj);
+            const float4 Z = *reinterpret_cast<const float4 *>(sz + jj);
+            const float4 M = *reinterpret_cast<const float4 *>(sm + jj);
+            pair2<IR, GUARD>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(M.x, M.y), eps2, nx, ny,
+                             nz, ax, ay, az, ph);
+            pair2<IR, GUARD>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(M.z, M.w), eps2, nx, ny,
+                             nz, ax, ay, az, ph);
+        }
+#pragma unroll
+        for (int k = 0; k < IR; ++k) {
+            acc[k][0].add(ax[k].x + ax[k].y);
+            acc[k][1].add(ay[k].x + ay[k].y);
+            acc[k][2].add(az[k].x + az[k].y);
+            acc[k][3].add(ph[k].x + ph[k].y);
+        }
+
+        if (__syncthreads_or(!ok)) {
+            // A stage never arrived: latch the error, let the copies that are
+            // still in flight land (bounded), and leave together.
+            if (tid == 0) {
+                set_status(p.status, kStatusTimeout);
+                for (int64_t r = q; r < nq && r < q + ST; ++r)
+                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), p.timeout);
+            }
+            __syncthreads();
+            return;
+        }
+        if (tid == 0 && q + ST < nq) {
+            fence_proxy_async();
+            issue(q + ST);
+        }
+
+        if (jt == p.ntiles - 1 || q == nq - 1) {
+            // end of this CTA's segment of i-block b: tiles [seg_begin, jt]
+            if (seg_begin == 0 && jt == p.ntiles - 1) {
+                force_epilogue<NT, IR, POL, GUARD>(p, b, acc, mi);
+            } else {
+                const int slot = (b == first_block) ? 0 : 1;
+                Record *rec = p.records + (2 * c + slot) * BI;
+#pragma unroll
+                for (int k = 0; k < IR; ++k) store_record<POL>(rec + k * NT + tid, acc[k]);
+                __threadfence();
+                __syncthreads();
+                const int64_t cf = sk_owner(p.total, C, b * p.ntiles);
+                const int64_t cl = sk_owner(p.total, C, b * p.ntiles + p.ntiles - 1);
+                if (tid == 0) {
+                    const uint32_t prev = atomicAdd(&p.counters[b], 1u);
+                    s_last = (prev == (uint32_t)(cl - cf));
+                }
+                __syncthreads();
+                if (s_last) {
+                    __threadfence();
+#pragma unroll
+                    for (int k = 0; k < IR; ++k)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[k][e].zero();
+                    for (int64_t cc = cf; cc <= cl; ++cc) {
+                        const int sl = (b == sk_lo(p.total, C, cc) / p.ntiles) ? 0 : 1;
+                        const Record *r = p.records + (2 * cc + sl) * BI;
+#pragma unroll
+                        for (int k = 0; k < IR; ++k) merge_record<POL>(acc[k], r + k * NT + tid);
+                    }
+                    force_epilogue<NT, IR, POL, GUARD>(p, b, acc, mi);
+                    if (tid == 0) p.counters[b] = 0u;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ FP64 pairs
+// One i per thread, j-tiles of NT particles staged through shared memory by
+// the whole CTA; the pair j == i is skipped by index, and with eps == 0 so
+// are coincident pairs.
+template <int NT, bool GUARD>
+__global__ void __launch_bounds__(NT)
+    force_fp64_kernel(const double *__restrict__ pos, const double *__restrict__ mass, int64_t N,
+                      double eps2, double G, double *acc, double *pot, double *vel, double kick,
+                      uint32_t *status) {
+    __shared__ double sx[NT], sy[NT], sz[NT], sm[NT];
+    const int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
+    const bool live = i < N;
+    const double xi = live ? pos[3 * i] : 0.0;
+    const double yi = live ? pos[3 * i + 1] : 0.0;
+    const double zi = live ? pos[3 * i + 2] : 0.0;
+    double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+    for (int64_t j0 = 0; j0 < N; j0 += NT) {
+        const int64_t j = j0 + threadIdx.x;
+        if (j < N) {
+            sx[threadIdx.x] = pos[3 * j];
+            sy[threadIdx.x] = pos[3 * j + 1];
+            sz[threadIdx.x] = pos[3 * j + 2];
+            sm[threadIdx.x] = mass[j];
+        }
+        __syncthreads();
+        const int nj = (int)((N - j0) < NT ? (N - j0) : NT);
+        for (int jj = 0; jj < nj; ++jj) {
+            if (j0 + jj == i) continue;
+            const double dx = sx[jj] - xi, dy = sy[jj] - yi, dz = sz[jj] - zi;
+            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+            if (GUARD && r2 == 0.0) continue;
+            const double ri = rsqrt(r2);
+            const double s = sm[jj] * ri;
+            const double s3 = s * (ri * ri);
+            ax = fma(s3, dx, ax);
+            ay = fma(s3, dy, ay);
+            az = fma(s3, dz, az);
+            ph += s;
+        }
+        __syncthreads();
+    }
+    if (live) {
+        const double gx = G * ax, gy = G * ay, gz = G * az, gp = -G * ph;
+        acc[3 * i] = gx;
+        acc[3 * i + 1] = gy;
+        acc[3 * i + 2] = gz;
+        if (pot) pot[i] = gp;
+        if (vel) {
+            vel[3 * i] += kick * gx;
+            vel[3 * i + 1] += kick * gy;
+            vel[3 * i + 2] += kick * gz;
+        }
+        if (!(isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(gp)))
+            dev::set_status(status, kStatusNonFinite);
+    }
+}
+
+// ---------------------------------------------------------- dispatch
+// Shapes compiled into this build: (threads, i per thread, tile_j, stages).
+#define NB_FORCE_SHAPES(X) \
+    X(256, 4, 256, 3)      \
+    X(256, 2, 256, 3)      \
+    X(128, 2, 128, 3)      \
+    X(128, 1, 64, 2)
+
+bool force_shape_compiled(const Shape &s) {
+#define NB_MATCH(NT, IR, TJ, ST) \
+    if (s.threads == NT && s.ipt == IR && s.tile_j == TJ && s.stages == ST) return true;
+    NB_FORCE_SHAPES(NB_MATCH)
+#undef NB_MATCH
+    return false;
+}
+
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD>
+static int launch_sk(const ForceParams &p, int grid, cudaStream_t st) {
+    auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD>;
+    const size_t smem = (size_t)ST * 16 * TJ + (size_t)ST * 8;
+    kern<<<grid, NT, smem, st>>>(p);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <int NT, int IR, int TJ, int ST>
+static int launch_sk_pol(const ForceParams &p, int pol, bool guard, int grid, cudaStream_t st) {
+    switch (pol * 2 + (guard ? 1 : 0)) {
+        case NB_PREC_FP32 * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_FP32, false>(p, grid, st);
+        case NB_PREC_FP32 * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_FP32, true>(p, grid, st);
+        case NB_PREC_KAHAN * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_KAHAN, false>(p, grid, st);
+        case NB_PREC_KAHAN * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_KAHAN, true>(p, grid, st);
+        case NB_PREC_F64ACC * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_F64ACC, false>(p, grid, st);
+        case NB_PREC_F64ACC * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_F64ACC, true>(p, grid, st);
+    }
+    return fail(NB_ERR_UNSUPPORTED, "precision %d has no FP32-pair kernel", pol);
+}
+
+int64_t force_grid(const Shape &sh, int64_t total) {
+    const int64_t slots = (int64_t)sh.ctas_per_sm * device_sm_count();
+    return std::max<int64_t>(1, std::min<int64_t>(slots, total));
+}
+
+int launch_force(const ForceJob &j) {
+    const bool guard = (j.eps == 0.0);
+    uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
+    if (j.precision == NB_PREC_FP64) {
+        constexpr int NT = 128;
+        const int64_t grid = cdiv(j.N, NT);
+        if (guard)
+            force_fp64_kernel<NT, true><<<(unsigned)grid, NT, 0, j.stream>>>(
+                j.pos, j.mass, j.N, 0.0, j.G, j.acc, j.pot, j.vel, j.kick, status);
+        else
+            force_fp64_kernel<NT, false><<<(unsigned)grid, NT, 0, j.stream>>>(
+                j.pos, j.mass, j.N, j.eps * j.eps, j.G, j.acc, j.pot, j.vel, j.kick, status);
+        NB_CUDA(cudaGetLastError());
+        return NB_OK;
+    }
+    float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
+    if (!j.packed_ready) {
+        int rc = launch_pack(j.pos, j.mass, j.N, j.L.Np, soa, j.stream);
+        if (rc) return rc;
+    }
+    const Shape &sh = j.shape;
+    ForceParams p;
+    p.soa = soa;
+    p.Np = j.L.Np;
+    p.N = j.N;
+    p.nblocks = (int32_t)cdiv(j.N, sh.block_i());
+    p.ntiles = (int32_t)cdiv(j.N, sh.tile_j);
+    p.total = (int64_t)p.nblocks * p.ntiles;
+    const float eps_f = (float)j.eps;
+    p.eps2 = eps_f * eps_f;
+    p.G = j.G;
+    p.acc = j.acc;
+    p.pot = j.pot;
+    p.vel = j.vel;
+    p.kick = j.kick;
+    p.records = reinterpret_cast<Record *>(j.ws + j.L.records);
+    p.counters = reinterpret_cast<uint32_t *>(j.ws + j.L.counters);
+    p.status = status;
+    p.timeout = j.timeout;
+    const int grid = (int)force_grid(sh, p.total);
+#define NB_DISPATCH(NT, IR, TJ, ST)                                                   \
+    if (sh.threads == NT && sh.ipt == IR && sh.tile_j == TJ && sh.stages == ST)      \
+        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, grid, j.stream);
+    NB_FORCE_SHAPES(NB_DISPATCH)
+#undef NB_DISPATCH
+    return fail(NB_ERR_UNSUPPORTED, "force kernel shape (%d,%d,%d,%d) not compiled", sh.threads,
+                sh.ipt, sh.tile_j, sh.stages);
+}
+
+}  // namespace nb

@@ -1,0 +1,165 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the ABI: the public surface is include/nbody.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbody.h"
+
+namespace nb {
+
+// ---------------------------------------------------------------- errors
+// Records a message for nb_last_error() and returns `code`.
+int fail(int code, const char *fmt, ...);
+void clear_error();
+int cuda_check(cudaError_t e, const char *what);
+#define NB_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return nb::cuda_check(e_, #call); \
+    } while (0)
+
+// Device status word bits (latched with atomicOr, read by nb_poll_status).
+constexpr uint32_t kStatusTimeout = 1u << NB_ERR_TIMEOUT;
+constexpr uint32_t kStatusNonFinite = 1u << NB_ERR_NONFINITE;
+constexpr uint32_t kStatusInvalid = 1u << NB_ERR_INVALID;
+
+constexpr long long kDefaultTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------- launch shapes
+// Shape of the FP32-pair stream-K force kernels (nb_tune resolved).
+struct Shape {
+    int threads;      // NT
+    int ipt;          // i-particles per thread (IR)
+    int tile_j;       // TJ
+    int stages;       // ST
+    int ctas_per_sm;  // persistent CTAs per SM
+    int block_i() const { return threads * ipt; }
+};
+
+// Shape used for N particles when the caller gives no (or a partial) tune.
+Shape default_shape(int64_t N, int precision, int kind);
+// Resolves opts->tune against the defaults; returns false if not compiled.
+bool resolve_shape(const nb_opts *opts, int64_t N, int kind, Shape *out);
+bool shape_compiled(const Shape &s, int kind);
+enum Kind { kKindForce = 0, kKindVjp = 1 };
+
+int device_sm_count();
+
+// --------------------------------------------------------- workspace
+// Byte offsets inside the caller's workspace.  Everything is 256-B aligned.
+struct WsLayout {
+    size_t status;    // uint32 status word (+ padding to 256 B)
+    size_t counters;  // uint32 arrival counters, one per i-block
+    size_t packA;     // float SoA [4][Np]: x, y, z, m of the j-particles
+    size_t packB;     // float SoA [4][Np]: VJP cotangent side (cx, cy, cz, pbar)
+    size_t records;   // stream-K partial records
+    size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
+    size_t total;
+    int64_t Np;       // padded particle count of the pack arrays
+    int64_t max_blocks;
+    int64_t max_grid;
+    int64_t record_bytes_per_i;
+};
+
+WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts);
+int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Stream-K split: CTA c of C owns linear work items [lo(c), lo(c+1)) of T.
+__host__ __device__ inline int64_t sk_lo(int64_t T, int64_t C, int64_t c) { return T * c / C; }
+// The CTA whose range holds item t (0 <= t < T).
+__host__ __device__ inline int64_t sk_owner(int64_t T, int64_t C, int64_t t) {
+    return ((t + 1) * C - 1) / T;
+}
+
+// ----------------------------------------------------- kernel launchers
+struct ForceJob {
+    const double *pos;
+    const double *mass;
+    int64_t N;
+    double eps;
+    double G;
+    double *acc;
+    double *pot;
+    // optional fused closing half-kick: vel += kick * acc
+    double *vel;
+    double kick;
+    int precision;
+    bool packed_ready;  // packA already holds float positions of `pos`
+    long long timeout;
+    cudaStream_t stream;
+    char *ws;
+    WsLayout L;
+    Shape shape;
+};
+
+int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
+                cudaStream_t st);
+int launch_force(const ForceJob &job);
+
+struct VjpJob {
+    const double *pos;
+    const double *mass;
+    int64_t N;
+    double eps;
+    double G;
+    // cotangent inputs (nb_forces_vjp form) ...
+    const double *acc_bar;
+    const double *pot_bar;
+    // ... or the step-adjoint form: c = kick_coef * (vel_bar += drift_dt * pos_bar)
+    bool step_form;
+    double drift_dt;
+    double kick_coef;
+    double *vel_bar;
+    // outputs
+    double *pos_bar;
+    double *mass_bar;
+    bool accumulate;  // add into pos_bar/mass_bar instead of overwriting
+    // optional fused force + reverse drift (nb_step_vjp_reverse)
+    double *acc_out;
+    double *vhalf;
+    double *pos_rw;
+    double rewind_kick;
+    double rewind_drift;
+    int precision;
+    long long timeout;
+    cudaStream_t stream;
+    char *ws;
+    WsLayout L;
+    Shape shape;
+};
+int launch_vjp(const VjpJob &job);
+
+int launch_kick_drift_pack(double *pos, double *vel, const double *acc, const double *mass,
+                           int64_t N, int64_t Np, double dt, float *soa, cudaStream_t st);
+int launch_energy(const double *vel, const double *mass, const double *pot, int64_t N,
+                  double *out3, char *ws, const WsLayout &L, cudaStream_t st);
+
+struct BatchedJob {
+    const double *mass;
+    const int64_t *offsets;
+    int32_t B;
+    const double *eps;
+    double G;
+    double *pos;
+    double *vel;
+    double *acc;
+    double *pot;
+    int64_t N;
+    double dt;
+    int64_t nsteps;   // 0 = forces only
+    bool acc_valid;
+    int precision;
+    long long timeout;
+    cudaStream_t stream;
+    char *ws;
+    WsLayout L;
+};
+int launch_batched(const BatchedJob &job);
+size_t batched_scratch_bytes(int32_t B);
+
+}  // namespace nb

@@ -1,0 +1,138 @@
+"""CPU-only checks of the C ABI: the library loads, exports every entry point
+declared in include/nbody.h, and rejects bad arguments on the host before
+touching a device (no GPU is needed for any of these calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import paper_2605_02744_gb300 as pkg
+    pkg.build()
+    from paper_2605_02744_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nbody.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = _declared()
+    assert len(names) >= 13
+    lib = B.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.EXPORTED) == names
+
+
+def test_version_and_defaults(B):
+    assert "sm_103a" in B.nb_version()
+    o = B.nb_opts()
+    B.lib().nb_opts_default(ctypes.byref(o))
+    assert o.precision == B.NB_PREC_F64ACC and o.G == 1.0 and o.stream is None
+    assert o.use_graph == 0 and not o.tune and o.timeout_cycles == 0
+
+
+def _opts(B, **kw):
+    o = B.nb_opts()
+    B.lib().nb_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def test_workspace_sizes(B):
+    o = _opts(B)
+    assert B.nb_workspace_bytes(0, 1, o) == 0
+    assert B.nb_workspace_bytes(10, 0, o) == 0
+    sizes = [B.nb_workspace_bytes(n, 1, o) for n in (1, 1000, 100000, 1 << 20)]
+    assert all(s % 256 == 0 for s in sizes)
+    assert sizes == sorted(sizes)
+    # the packed copy alone needs 32 B per (padded) particle
+    assert sizes[-1] >= 32 * (1 << 20)
+
+
+def test_tune_validation(B):
+    assert B.nb_tune_valid({"threads": 256, "i_per_thread": 4, "tile_j": 256, "stages": 3})
+    assert B.nb_tune_valid({"threads": 128, "i_per_thread": 1, "tile_j": 64, "stages": 2})
+    assert not B.nb_tune_valid({"threads": 96, "i_per_thread": 4, "tile_j": 256, "stages": 3})
+    assert not B.nb_tune_valid({"threads": 256, "i_per_thread": 4, "tile_j": 256, "stages": 3,
+                                "ctas_per_sm": 9})
+
+
+FAKE = 1 << 20  # an aligned non-NULL address; never dereferenced by these calls
+
+
+def _forces(B, N=16, eps=0.1, pos=FAKE, mass=FAKE, acc=FAKE, pot=None, ws=FAKE, wsb=None,
+            opts=None):
+    opts = opts or _opts(B)
+    if wsb is None:
+        wsb = B.nb_workspace_bytes(max(N, 1), 1, opts)
+    return B.lib().nb_forces(pos, mass, N, eps, acc, pot, ws, wsb, ctypes.byref(opts))
+
+
+@pytest.mark.parametrize("kw,code", [
+    ({"N": 0}, 1), ({"N": -5}, 1), ({"eps": -1.0}, 1), ({"eps": float("nan")}, 1),
+    ({"eps": float("inf")}, 1), ({"eps": 1e-30}, 1), ({"pos": None}, 1), ({"mass": None}, 1),
+    ({"acc": None}, 1), ({"pos": FAKE + 4}, 1), ({"pot": FAKE + 2}, 1), ({"ws": None}, 1),
+    ({"ws": FAKE + 16}, 1), ({"wsb": 1024}, 3),
+])
+def test_nb_forces_rejects_bad_arguments(B, kw, code):
+    assert _forces(B, **kw) == code
+    assert B.nb_last_error() != ""
+
+
+def test_bad_opts(B):
+    assert _forces(B, opts=_opts(B, precision=7)) == B.NB_ERR_INVALID
+    assert _forces(B, opts=_opts(B, G=float("inf"))) == B.NB_ERR_INVALID
+    assert _forces(B, opts=_opts(B, timeout_cycles=-1)) == B.NB_ERR_INVALID
+    bad = B.nb_tune(threads=96, i_per_thread=4, tile_j=256, stages=3, ctas_per_sm=1)
+    o = _opts(B)
+    o.tune = ctypes.pointer(bad)
+    assert _forces(B, opts=o) == B.NB_ERR_UNSUPPORTED
+    assert B.lib().nb_forces(FAKE, FAKE, 16, 0.1, FAKE, None, FAKE, 1 << 30, None) == 1
+
+
+def test_step_and_vjp_argument_checks(B):
+    o = _opts(B)
+    st = B.nb_state()
+    st.N, st.B = 16, 1
+    st.pos = st.vel = st.mass = st.acc = FAKE
+    st.ws, st.ws_bytes = FAKE, B.nb_workspace_bytes(16, 1, o)
+    lib = B.lib()
+    assert lib.nb_step(None, 1e-3, 1, ctypes.byref(o)) == 1
+    assert lib.nb_step(ctypes.byref(st), float("nan"), 1, ctypes.byref(o)) == 1
+    assert lib.nb_step(ctypes.byref(st), 1e-3, -1, ctypes.byref(o)) == 1
+    st.vel = None
+    assert lib.nb_step(ctypes.byref(st), 1e-3, 1, ctypes.byref(o)) == 1
+    st.vel = FAKE
+    st.B = 4  # batched without offsets
+    assert lib.nb_step(ctypes.byref(st), 1e-3, 1, ctypes.byref(o)) == 1
+    wsb = st.ws_bytes
+    assert lib.nb_forces_vjp(FAKE, FAKE, 16, 0.1, None, None, FAKE, FAKE, FAKE, wsb,
+                             ctypes.byref(o)) == 1
+    assert lib.nb_step_vjp(FAKE, FAKE, 16, 0.1, float("inf"), 0.5, FAKE, FAKE, FAKE, FAKE, wsb,
+                           ctypes.byref(o)) == 1
+    assert lib.nb_step_vjp(FAKE, FAKE, 16, 0.1, 1e-3, 5e-4, FAKE, None, FAKE, FAKE, wsb,
+                           ctypes.byref(o)) == 1
+    assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 0, FAKE, FAKE, None, FAKE, 1 << 30,
+                                 ctypes.byref(o)) == 1
+    assert lib.nb_energy(ctypes.byref(st), None, ctypes.byref(o)) == 1
+    assert lib.nb_poll_status(None, 0, None) == 1
+
+
+def test_python_binding_requires_cuda_tensors(B):
+    import torch
+    o = _opts(B)
+    x = torch.zeros((4, 3), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        B.nb_forces(x, x[:, 0].contiguous(), 0.1, x, None, torch.zeros(256, dtype=torch.uint8), o)

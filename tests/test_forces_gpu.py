@@ -1,0 +1,132 @@
+"""GPU parity of nb_forces against the FP64 oracle (element by element).
+
+Covers the four precision policies, ragged and tiny N (tail tiles, partial
+i-blocks, N = 1), the guarded eps = 0 kernel, every compiled launch shape,
+G scaling, run-to-run bitwise determinism, and the 2^20-particle workload on
+sampled rows computed exactly by the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_02744_gb300 import api, binding, ics
+from tests.gpu_util import TOL, dev, host, rel_err, rel_vec_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_2605_02744_gb300 as pkg
+    pkg.build()
+    oracle.build()
+    binding.lib()
+
+
+def _check(s, eps, prec, tol=None, G=1.0, tune=None):
+    a, p = api.forces(dev(s.pos), dev(s.mass), eps, precision=prec, G=G, tune=tune)
+    ra, rp = oracle.forces(s.pos, s.mass, eps, G)
+    ea = rel_vec_err(host(a), ra)
+    ep = rel_err(host(p), rp)
+    tol = TOL[prec] if tol is None else tol
+    assert ea.max() <= tol and ep.max() <= tol, (prec, s.n, ea.max(), ep.max())
+    return ea, ep
+
+
+@pytest.mark.parametrize("prec", ["fp32", "kahan", "f64acc", "fp64"])
+def test_plummer_1024_all_policies(prec):
+    _check(ics.plummer(1024, seed=0), 0.01, prec)
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 63, 64, 65, 127, 129, 1000, 2047, 2049, 5000, 8191,
+                               8193, 20001])
+def test_ragged_sizes(n):
+    s = ics.plummer(n, seed=n)
+    _check(s, 0.01, "f64acc")
+    if n <= 8193:
+        _check(s, 0.01, "kahan")
+
+
+@pytest.mark.parametrize("n", [3, 129, 4099])
+def test_ragged_sizes_fp64(n):
+    _check(ics.plummer_lognormal(n, seed=n), 0.02, "fp64")
+
+
+@pytest.mark.parametrize("prec", ["kahan", "f64acc", "fp64", "fp32"])
+def test_single_particle_is_exactly_zero(prec):
+    a, p = api.forces(dev([[0.3, -0.2, 0.1]]), dev([2.0]), 0.01, precision=prec)
+    assert np.all(host(a) == 0.0) and np.all(host(p) == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["f64acc", "kahan", "fp64"])
+def test_eps_zero_guarded_kernel(prec):
+    # coincident pair + separated particles, eps = 0: coincident pairs skipped
+    pos = np.array([[0.25, 0.5, -1.0], [0.25, 0.5, -1.0], [3.0, 4.0, 0.0], [0.0, 0.0, 0.0]])
+    mass = np.array([0.5, 0.75, 2.0, 1.0])
+    a, p = api.forces(dev(pos), dev(mass), 0.0, precision=prec)
+    ra, rp = oracle.forces(pos, mass, 0.0)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert np.all(np.isfinite(host(a))) and np.all(np.isfinite(host(p)))
+    assert rel_vec_err(host(a), ra).max() <= tol and rel_err(host(p), rp).max() <= tol
+
+
+def test_hand_worked_two_body_on_gpu():
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    a, p = api.forces(dev(pos), dev([1.0, 2.0]), 0.0, precision="fp64")
+    np.testing.assert_allclose(host(a)[0], [0.048, 0.064, 0.0], rtol=1e-15, atol=1e-18)
+    np.testing.assert_allclose(host(p), [-0.4, -0.2], rtol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(256, 4, 256, 3), (256, 2, 256, 3), (128, 2, 128, 3),
+                                   (128, 1, 64, 2)])
+@pytest.mark.parametrize("cps", [1, 2, 4])
+def test_every_compiled_shape(shape, cps):
+    t = dict(threads=shape[0], i_per_thread=shape[1], tile_j=shape[2], stages=shape[3],
+             ctas_per_sm=cps)
+    assert binding.nb_tune_valid(t)
+    s = ics.plummer(6000, seed=11)
+    _check(s, 0.01, "f64acc", tune=t)
+    _check(s, 0.01, "kahan", tune=t)
+
+
+def test_gravitational_constant():
+    _check(ics.plummer(3000, seed=2), 0.01, "f64acc", G=2.5)
+
+
+def test_bitwise_determinism():
+    s = ics.plummer(30000, seed=3)
+    outs = [api.forces(dev(s.pos), dev(s.mass), 1e-3, precision=p) for p in ("kahan", "kahan")]
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    outs = [api.forces(dev(s.pos), dev(s.mass), 1e-3, precision="f64acc") for _ in range(2)]
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_lognormal_65536_three_variants():
+    s = ics.plummer_lognormal(65536, seed=0)
+    rows = np.concatenate([np.random.default_rng(4).choice(s.n, 2048, replace=False),
+                           np.argsort(np.linalg.norm(s.pos, axis=1))[:64]])
+    ra, rp = oracle.forces_rows(s.pos, s.mass, 1e-3, rows)
+    for prec in ("f64acc", "kahan", "fp64", "fp32"):
+        a, p = api.forces(dev(s.pos), dev(s.mass), 1e-3, precision=prec)
+        ea = rel_vec_err(host(a)[rows], ra).max()
+        ep = rel_err(host(p)[rows], rp).max()
+        if prec != "fp32":
+            assert ea <= TOL[prec] and ep <= TOL[prec], (prec, ea, ep)
+
+
+@pytest.mark.parametrize("prec", ["kahan", "f64acc"])
+def test_plummer_2pow20_sampled_rows(prec):
+    # the 2^20-particle evaluation in the benchmark's launch shape; exact
+    # oracle rows for 1024 random particles plus the 64 innermost/outermost
+    n = 1 << 20
+    s = ics.plummer(n, seed=0)
+    r = np.linalg.norm(s.pos, axis=1)
+    order = np.argsort(r)
+    rows = np.unique(np.concatenate([np.random.default_rng(4).choice(n, 1024, replace=False),
+                                     order[:64], order[-64:]]))
+    a, p = api.forces(dev(s.pos), dev(s.mass), 1e-3, precision=prec)
+    ra, rp = oracle.forces_rows(s.pos, s.mass, 1e-3, rows)
+    ea = rel_vec_err(host(a)[rows], ra)
+    ep = rel_err(host(p)[rows], rp)
+    assert ea.max() <= 1e-5 and ep.max() <= 1e-5, (ea.max(), ep.max())
