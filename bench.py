@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the direct N-body hot path on GB300.
+
+Metric: G pair-interactions/s on a 2^20-particle Plummer sphere (eps = 1e-3,
+FP32 pairs with Kahan-compensated accumulation), one step = one kick-drift-kick
+leapfrog step through nb_step (kick + drift + FP32 pack, the all-pairs
+force + potential kernel with the closing half-kick fused into its epilogue)
+followed by nb_energy.  Interactions are counted as N^2 per step (the self
+pair is evaluated).  Alongside: the FP64-accumulate variant's rate, the
+adjoint/forward time ratio of the 16384-particle, 200-step gradient, the
+roofline of the force kernel against the FP32 FMA peak (20 flops per
+interaction), the end-to-end rate from host buffers, and the FP64 oracle timed
+on the host cores on a sample of rows.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica (no data exchange:
+the single-system workload does not shard without an all-gather, which this
+library does not implement), value = all ranks' interactions / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G pair-interactions/s at N=2^20 vs FP32 roofline; adjoint/forward time at 1e-5 err"
+UNIT = "G pair-interactions/s"
+N_MAIN = 1 << 20
+EPS_MAIN = 1e-3
+DT_MAIN = 1e-4
+FLOPS_PER_INTERACTION = 20
+FP32_LANES_PER_SM = 128
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_sk_plummer_2p20_traffic.txt")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        load = [float(r[1]) for r in rows if float(r[3]) > 200.0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def _traffic():
+    """DRAM bytes per force launch from the committed ncu summary, or None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_launch:"):
+                    return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """FP64 oracle rows on the host cores: exact a_i, phi_i for sampled i."""
+    import numpy as np
+
+    import oracle
+    from paper_2605_02744_gb300 import ics
+    oracle.build()
+    s = ics.plummer(N_MAIN, seed=0)
+    rng = np.random.default_rng(4)
+    t0 = time.perf_counter()
+    probe = rng.choice(N_MAIN, 64, replace=False)
+    oracle.forces_rows(s.pos, s.mass, EPS_MAIN, probe)
+    dt = time.perf_counter() - t0
+    nrows = int(max(64, min(N_MAIN, 64 * seconds / max(dt, 1e-3))))
+    rows = rng.choice(N_MAIN, nrows, replace=False)
+    t0 = time.perf_counter()
+    oracle.forces_rows(s.pos, s.mass, EPS_MAIN, rows)
+    el = time.perf_counter() - t0
+    rate = nrows * N_MAIN / el / 1e9
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nrows} exact rows x {N_MAIN} j of the 2^20 Plummer sphere "
+                      f"(FP64 C, OpenMP over rows), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_2605_02744_gb300 import ics
+    oracle.build()
+    s = ics.plummer(N_MAIN, seed=0)
+    rng = np.random.default_rng(4)
+    rows_per_step = 512
+    for _ in range(args.warmup):
+        oracle.forces_rows(s.pos, s.mass, EPS_MAIN, rng.choice(N_MAIN, rows_per_step, False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forces_rows(s.pos, s.mass, EPS_MAIN, rng.choice(N_MAIN, rows_per_step, False))
+    el = time.perf_counter() - t0
+    value = args.steps * rows_per_step * N_MAIN / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Plummer N=2^20, eps=1e-3, force+potential rows "
+                                   f"({rows_per_step} sampled i x all j per step)",
+                       "N": N_MAIN},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{rows_per_step} exact rows per step x {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_steps(system, dt, steps, flush, torch):
+    """Per-step CUDA-event times (ms) on the library's stream, L2 flushed in between."""
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        system.step(dt, 1)
+        system.energy()
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def adjoint_ratio(torch):
+    """Forward (200 KDK steps) vs gradient time at the 16384-particle workload."""
+    from paper_2605_02744_gb300 import adjoint, ics
+    s = ics.plummer(16384, seed=0)
+    target = ics.perturb_positions(s.pos, 1e-3, seed=2)
+    return adjoint.time_forward_backward(s, target, eps=5e-3, dt=1e-3, nsteps=200, segment=20,
+                                         precision="f64acc")
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import paper_2605_02744_gb300 as pkg
+    from paper_2605_02744_gb300 import api, binding, ics
+    pkg.build()
+    s = ics.plummer(N_MAIN, seed=0)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    results = {}
+    for prec in ("kahan", "f64acc"):
+        system = api.System(s.pos, s.vel, s.mass, EPS_MAIN, precision=prec, device=dev)
+        system.forces()
+        for _ in range(args.warmup):
+            system.step(DT_MAIN, 1)
+            system.energy()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index or 0) as clk:
+            times = _time_steps(system, DT_MAIN, args.steps, flush, torch)
+        torch.cuda.synchronize()
+        assert system.poll() == binding.NB_OK
+        results[prec] = (times, clk.summary())
+        del system
+        torch.cuda.empty_cache()
+
+    times, clocks = results["kahan"]
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    inter = float(N_MAIN) * N_MAIN
+    value = ws * args.steps * inter / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public API from pinned host buffers
+    host = {k: torch.as_tensor(getattr(s, k)).pin_memory() for k in ("pos", "vel", "mass")}
+    e2e_sys = api.System(s.pos, s.vel, s.mass, EPS_MAIN, precision="kahan", device=dev)
+    outs = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
+            for k, v in (("pos", e2e_sys.pos), ("vel", e2e_sys.vel), ("acc", e2e_sys.acc),
+                         ("pot", e2e_sys.pot))}
+    eh = torch.empty(3, dtype=torch.float64, pin_memory=True)
+    st = torch.cuda.current_stream()
+
+    def e2e_step():
+        e2e_sys.pos.copy_(host["pos"], non_blocking=True)
+        e2e_sys.vel.copy_(host["vel"], non_blocking=True)
+        e2e_sys.mass.copy_(host["mass"], non_blocking=True)
+        e2e_sys.state.acc_valid = 0
+        e2e_sys.step(DT_MAIN, 1)
+        eh.copy_(e2e_sys.energy(), non_blocking=True)
+        for k in ("pos", "vel", "acc", "pot"):
+            outs[k].copy_(getattr(e2e_sys, k), non_blocking=True)
+        st.synchronize()
+
+    e2e_step()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_el = time.perf_counter() - t0
+    # two force evaluations per e2e step (priming + step) on fresh host state
+    e2e_value = ws * e2e_steps * 2 * inter / e2e_el / 1e9
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = sum(v.numel() * 8 for v in outs.values()) + 24
+    del e2e_sys
+
+    adj = None
+    if not args.skip_adjoint:
+        try:
+            adj = adjoint_ratio(torch)
+        except Exception as e:  # reported, never silently replaced
+            adj = {"error": f"{type(e).__name__}: {e}"}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks = _peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    step_ms = statistics.mean(times)
+    achieved = FLOPS_PER_INTERACTION * inter / (step_ms * 1e-3) / 1e12
+    obs = clocks.get("sm_mhz")
+    traffic = _traffic()
+    f64_ms = statistics.mean(results["f64acc"][0])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Plummer sphere N=2^20 (1048576), equal mass, seed 0, eps=1e-3; "
+                               "one KDK step dt=1e-4 (FP32 pairs, Kahan accumulation, FP64 "
+                               "state) + energy",
+                   "N": N_MAIN, "precision": "kahan", "interactions_per_step": "N^2",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "force_sk_kernel<256,4,256,3,KAHAN>",
+                     "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                   f"{max_mhz:.0f} MHz (max SM clock)",
+                     "frac_at_observed_clock": (achieved / (peak_tflops * obs / max_mhz)
+                                                if obs else None),
+                     "timing": "CUDA events around each nb_step+nb_energy (force kernel "
+                               "plus O(N) kernels) on the launching stream"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "how": "pinned host pos/vel/mass -> device, nb_step (priming force + 1 KDK "
+                       "step), nb_energy, pos/vel/acc/pot/energy -> host; wall clock"},
+        "gpu_launches": 4 * args.steps,
+        "variants": {"f64acc_value": ws * args.steps * inter / (sum(results["f64acc"][0]) * 1e-3)
+                     / 1e9, "f64acc_ms_per_step": f64_ms,
+                     "kahan_ms_per_step": step_ms},
+        "adjoint": adj,
+    }
+    if ws == 1 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -65,6 +65,20 @@ typedef enum {
     NB_PREC_FP64 = 3    /* FP64 pairs and sums                                */
 } nb_precision;
 
+/* How the FP32-pair kernels form the displacement x_j - x_i.  SPLIT keeps
+ * each coordinate as an unevaluated sum hi + lo of two floats (hi = x
+ * rounded to FP32, lo = the rounding remainder) and forms
+ * (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo), so close pairs far from the
+ * origin keep ~1e-7 relative accuracy (6 more FP32 operations per pair).
+ * SINGLE rounds positions to FP32 once, as the paper's device kernel does
+ * (Sec. 3.1); its displacement error is ~6e-8 |x| / |x_j - x_i|, which
+ * reaches ~1e-4 relative acceleration error for close pairs at N = 2^20. */
+typedef enum {
+    NB_POS_DEFAULT = 0, /* SPLIT for KAHAN and F64ACC, SINGLE for FP32      */
+    NB_POS_SPLIT = 1,
+    NB_POS_SINGLE = 2
+} nb_positions;
+
 /* Launch shape of the FP32-pair kernels.  Zero fields take the built-in
  * defaults for the problem size; nb_tune_valid() reports whether a shape
  * is one this build was compiled for. */
@@ -84,10 +98,11 @@ typedef struct nb_opts {
     const nb_tune *tune;    /* NULL = defaults                                 */
     int64_t timeout_cycles; /* bound on every device wait, in SM clock cycles;
                                0 = default (about 2 s)                         */
+    int32_t positions;      /* nb_positions (ignored by NB_PREC_FP64)          */
 } nb_opts;
 
 /* Fills *opts with precision F64ACC, G = 1, default stream, no graph,
- * default tune and timeout. */
+ * default tune, timeout and position handling. */
 void nb_opts_default(nb_opts *opts);
 
 /* Library version string and the list of compiled kernel shapes. */

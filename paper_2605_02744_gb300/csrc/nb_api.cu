@@ -102,9 +102,9 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     L.counters = off;
     off = align256(off + sizeof(uint32_t) * (size_t)L.max_blocks);
     L.packA = off;
-    off = align256(off + 16 * (size_t)L.Np);
+    off = align256(off + 4 * kPackArrays * (size_t)L.Np);
     L.packB = off;
-    off = align256(off + 16 * (size_t)L.Np);
+    off = align256(off + 32 * (size_t)L.Np);
     L.records = off;
     off = align256(off + 2 * (size_t)L.max_grid * (size_t)L.record_bytes_per_i);
     L.scratch = off;
@@ -120,6 +120,12 @@ int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L) {
         return fail(NB_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes,
                     L.total);
     return NB_OK;
+}
+
+bool positions_split(const nb_opts *o) {
+    if (o->positions == NB_POS_SPLIT) return true;
+    if (o->positions == NB_POS_SINGLE) return false;
+    return o->precision != NB_PREC_FP32;
 }
 
 // ------------------------------------------------------------ checks
@@ -140,6 +146,8 @@ static int check_common(const nb_opts *o, int64_t N, double eps) {
     if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
         return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
     if (o->timeout_cycles < 0) return fail(NB_ERR_INVALID, "timeout_cycles must be >= 0");
+    if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_SINGLE)
+        return fail(NB_ERR_INVALID, "unknown positions mode %d", o->positions);
     return NB_OK;
 }
 
@@ -175,6 +183,7 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     j->vel = nullptr;
     j->kick = 0.0;
     j->precision = o->precision;
+    j->split = positions_split(o);
     j->packed_ready = false;
     j->timeout = timeout_of(o);
     j->stream = (cudaStream_t)o->stream;
@@ -371,6 +380,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
         key.o.stream = o->stream;
         key.o.use_graph = o->use_graph;
         key.o.timeout_cycles = o->timeout_cycles;
+        key.o.positions = o->positions;
         if (o->tune) {
             key.t.threads = o->tune->threads;
             key.t.i_per_thread = o->tune->i_per_thread;

@@ -28,23 +28,26 @@ using dev::Acc;
 using dev::Record;
 
 // ------------------------------------------------------------------ pack
-// FP64 [N][3] positions + [N] masses -> float SoA x[Np] y[Np] z[Np] m[Np],
-// round-to-nearest; entries N..Np-1 are zero-mass particles at the origin.
+// FP64 [N][3] positions + [N] masses -> float SoA of 7 arrays of Np:
+//   x.hi y.hi z.hi m x.lo y.lo z.lo
+// hi = the coordinate rounded to nearest FP32, lo = (x - hi) rounded to
+// FP32 (the split "double-single" representation); entries N..Np-1 are
+// zero-mass particles at the origin.
 __global__ void pack_soa_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
                                 int64_t N, int64_t Np, float *__restrict__ soa) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float x = 0.f, y = 0.f, z = 0.f, m = 0.f;
+        float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f}, m = 0.f;
         if (i < N) {
-            x = __double2float_rn(pos[3 * i]);
-            y = __double2float_rn(pos[3 * i + 1]);
-            z = __double2float_rn(pos[3 * i + 2]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double x = pos[3 * i + c];
+                hi[c] = __double2float_rn(x);
+                lo[c] = __double2float_rn(x - (double)hi[c]);
+            }
             m = __double2float_rn(mass[i]);
         }
-        soa[i] = x;
-        soa[Np + i] = y;
-        soa[2 * Np + i] = z;
-        soa[3 * Np + i] = m;
+        store_packed(soa, Np, i, hi, lo, m);
     }
 }
 
@@ -59,7 +62,7 @@ int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, fl
 
 // ----------------------------------------------------------- FP32 pairs
 struct ForceParams {
-    const float *soa;  // [4][Np]
+    const float *soa;  // [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
     int64_t Np;
     int64_t N;
     int64_t total;  // nblocks * ntiles
@@ -77,18 +80,27 @@ struct ForceParams {
     long long timeout;
 };
 
-template <int IR, bool GUARD>
+// Two j-particles (packed in the .x/.y halves) against IR i-particles.
+// The displacement is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) when SPLIT.
+template <int IR, bool GUARD, bool SPLIT>
 __device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const float2 zj,
+                                      const float2 xl, const float2 yl, const float2 zl,
                                       const float2 mj, const float2 eps2, const float2 (&nx)[IR],
                                       const float2 (&ny)[IR], const float2 (&nz)[IR],
-                                      float2 (&ax)[IR], float2 (&ay)[IR], float2 (&az)[IR],
-                                      float2 (&ph)[IR]) {
+                                      const float2 (&nxl)[IR], const float2 (&nyl)[IR],
+                                      const float2 (&nzl)[IR], float2 (&ax)[IR],
+                                      float2 (&ay)[IR], float2 (&az)[IR], float2 (&ph)[IR]) {
     using namespace dev;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
-        const float2 dx = add2(xj, nx[k]);
-        const float2 dy = add2(yj, ny[k]);
-        const float2 dz = add2(zj, nz[k]);
+        float2 dx = add2(xj, nx[k]);
+        float2 dy = add2(yj, ny[k]);
+        float2 dz = add2(zj, nz[k]);
+        if (SPLIT) {
+            dx = add2(dx, add2(xl, nxl[k]));
+            dy = add2(dy, add2(yl, nyl[k]));
+            dz = add2(dz, add2(zl, nzl[k]));
+        }
         float2 r2 = fma2(dx, dx, eps2);
         r2 = fma2(dy, dy, r2);
         r2 = fma2(dz, dz, r2);
@@ -137,14 +149,15 @@ __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
     if (bad) dev::set_status(p.status, kStatusNonFinite);
 }
 
-template <int NT, int IR, int TJ, int ST, int POL, bool GUARD>
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT>
 __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
     using namespace dev;
     constexpr int BI = NT * IR;
+    constexpr int NC = SPLIT ? 7 : 4;  // SoA arrays staged per j-tile
     static_assert(TJ % 4 == 0 && (TJ * 4) % 16 == 0, "tile must be 16-byte granular");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + ST * 16 * TJ);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + ST * NC * 4 * TJ);
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
@@ -163,17 +176,17 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
     auto issue = [&](int64_t q) {
         const int s = (int)(q % ST);
         const int64_t jt = (L0 + q) % p.ntiles;
-        float *dst = stages + s * 4 * TJ;
-        mbar_arrive_expect_tx(&full[s], 16 * TJ);
+        float *dst = stages + s * NC * TJ;
+        mbar_arrive_expect_tx(&full[s], NC * 4 * TJ);
 #pragma unroll
-        for (int comp = 0; comp < 4; ++comp)
+        for (int comp = 0; comp < NC; ++comp)
             bulk_g2s(dst + comp * TJ, p.soa + comp * p.Np + jt * TJ, 4 * TJ, &full[s]);
     };
     if (tid == 0) {
         for (int64_t q = 0; q < nq && q < ST; ++q) issue(q);
     }
 
-    float2 nx[IR], ny[IR], nz[IR];
+    float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR];
     float mi[IR];
     Acc<POL> acc[IR][4];
     const float2 eps2 = f2(p.eps2, p.eps2);
@@ -194,16 +207,28 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
                 nx[k] = f2(-x, -x);
                 ny[k] = f2(-y, -y);
                 nz[k] = f2(-z, -z);
+                if (SPLIT) {
+                    const float xl = p.soa[4 * p.Np + i], yl = p.soa[5 * p.Np + i],
+                                zl = p.soa[6 * p.Np + i];
+                    nxl[k] = f2(-xl, -xl);
+                    nyl[k] = f2(-yl, -yl);
+                    nzl[k] = f2(-zl, -zl);
+                } else {
+                    nxl[k] = nyl[k] = nzl[k] = f2(0.f, 0.f);
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[k][e].zero();
             }
         }
         const int s = (int)(q % ST);
         const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((q / ST) & 1), p.timeout);
-        const float *sx = stages + s * 4 * TJ;
+        const float *sx = stages + s * NC * TJ;
         const float *sy = sx + TJ;
         const float *sz = sx + 2 * TJ;
         const float *sm = sx + 3 * TJ;
+        const float *sxl = sx + (SPLIT ? 4 : 0) * TJ;
+        const float *syl = sx + (SPLIT ? 5 : 0) * TJ;
+        const float *szl = sx + (SPLIT ? 6 : 0) * TJ;
 
         float2 ax[IR], ay[IR], az[IR], ph[IR];
 #pragma unroll
@@ -214,10 +239,18 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
             const float4 Y = *reinterpret_cast<const float4 *>(sy + jj);
             const float4 Z = *reinterpret_cast<const float4 *>(sz + jj);
             const float4 M = *reinterpret_cast<const float4 *>(sm + jj);
-            pair2<IR, GUARD>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(M.x, M.y), eps2, nx, ny,
-                             nz, ax, ay, az, ph);
-            pair2<IR, GUARD>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(M.z, M.w), eps2, nx, ny,
-                             nz, ax, ay, az, ph);
+            float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
+            if (SPLIT) {
+                XL = *reinterpret_cast<const float4 *>(sxl + jj);
+                YL = *reinterpret_cast<const float4 *>(syl + jj);
+                ZL = *reinterpret_cast<const float4 *>(szl + jj);
+            }
+            pair2<IR, GUARD, SPLIT>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(XL.x, XL.y),
+                                    f2(YL.x, YL.y), f2(ZL.x, ZL.y), f2(M.x, M.y), eps2, nx, ny,
+                                    nz, nxl, nyl, nzl, ax, ay, az, ph);
+            pair2<IR, GUARD, SPLIT>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(XL.z, XL.w),
+                                    f2(YL.z, YL.w), f2(ZL.z, ZL.w), f2(M.z, M.w), eps2, nx, ny,
+                                    nz, nxl, nyl, nzl, ax, ay, az, ph);
         }
 #pragma unroll
         for (int k = 0; k < IR; ++k) {
@@ -354,24 +387,31 @@ bool force_shape_compiled(const Shape &s) {
     return false;
 }
 
-template <int NT, int IR, int TJ, int ST, int POL, bool GUARD>
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT>
 static int launch_sk(const ForceParams &p, int grid, cudaStream_t st) {
-    auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD>;
-    const size_t smem = (size_t)ST * 16 * TJ + (size_t)ST * 8;
+    auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT>;
+    const size_t smem = (size_t)ST * (SPLIT ? 7 : 4) * 4 * TJ + (size_t)ST * 8;
     kern<<<grid, NT, smem, st>>>(p);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
 
+template <int NT, int IR, int TJ, int ST, int POL>
+static int launch_sk_gs(const ForceParams &p, bool guard, bool split, int grid, cudaStream_t st) {
+    if (guard)
+        return split ? launch_sk<NT, IR, TJ, ST, POL, true, true>(p, grid, st)
+                     : launch_sk<NT, IR, TJ, ST, POL, true, false>(p, grid, st);
+    return split ? launch_sk<NT, IR, TJ, ST, POL, false, true>(p, grid, st)
+                 : launch_sk<NT, IR, TJ, ST, POL, false, false>(p, grid, st);
+}
+
 template <int NT, int IR, int TJ, int ST>
-static int launch_sk_pol(const ForceParams &p, int pol, bool guard, int grid, cudaStream_t st) {
-    switch (pol * 2 + (guard ? 1 : 0)) {
-        case NB_PREC_FP32 * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_FP32, false>(p, grid, st);
-        case NB_PREC_FP32 * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_FP32, true>(p, grid, st);
-        case NB_PREC_KAHAN * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_KAHAN, false>(p, grid, st);
-        case NB_PREC_KAHAN * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_KAHAN, true>(p, grid, st);
-        case NB_PREC_F64ACC * 2: return launch_sk<NT, IR, TJ, ST, NB_PREC_F64ACC, false>(p, grid, st);
-        case NB_PREC_F64ACC * 2 + 1: return launch_sk<NT, IR, TJ, ST, NB_PREC_F64ACC, true>(p, grid, st);
+static int launch_sk_pol(const ForceParams &p, int pol, bool guard, bool split, int grid,
+                         cudaStream_t st) {
+    switch (pol) {
+        case NB_PREC_FP32: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_FP32>(p, guard, split, grid, st);
+        case NB_PREC_KAHAN: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_KAHAN>(p, guard, split, grid, st);
+        case NB_PREC_F64ACC: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_F64ACC>(p, guard, split, grid, st);
     }
     return fail(NB_ERR_UNSUPPORTED, "precision %d has no FP32-pair kernel", pol);
 }
@@ -423,7 +463,7 @@ int launch_force(const ForceJob &j) {
     const int grid = (int)force_grid(sh, p.total);
 #define NB_DISPATCH(NT, IR, TJ, ST)                                                   \
     if (sh.threads == NT && sh.ipt == IR && sh.tile_j == TJ && sh.stages == ST)      \
-        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, grid, j.stream);
+        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, j.split, grid, j.stream);
     NB_FORCE_SHAPES(NB_DISPATCH)
 #undef NB_DISPATCH
     return fail(NB_ERR_UNSUPPORTED, "force kernel shape (%d,%d,%d,%d) not compiled", sh.threads,

@@ -52,8 +52,8 @@ int device_sm_count();
 struct WsLayout {
     size_t status;    // uint32 status word (+ padding to 256 B)
     size_t counters;  // uint32 arrival counters, one per i-block
-    size_t packA;     // float SoA [4][Np]: x, y, z, m of the j-particles
-    size_t packB;     // float SoA [4][Np]: VJP cotangent side (cx, cy, cz, pbar)
+    size_t packA;     // float SoA [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
+    size_t packB;     // float SoA [8][Np]: VJP cotangent side
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
     size_t total;
@@ -89,6 +89,7 @@ struct ForceJob {
     double *vel;
     double kick;
     int precision;
+    bool split;         // hi/lo displacement (nb_positions resolved)
     bool packed_ready;  // packA already holds float positions of `pos`
     long long timeout;
     cudaStream_t stream;
@@ -96,6 +97,24 @@ struct ForceJob {
     WsLayout L;
     Shape shape;
 };
+
+// Resolves nb_opts::positions for a precision: true = split hi/lo.
+bool positions_split(const nb_opts *opts);
+
+// Number of float arrays of Np entries in a packed position buffer.
+constexpr int kPackArrays = 7;
+
+// Writes particle i of the packed SoA: x.hi y.hi z.hi m x.lo y.lo z.lo.
+__host__ __device__ inline void store_packed(float *soa, int64_t Np, int64_t i, const float hi[3],
+                                             const float lo[3], float m) {
+    soa[i] = hi[0];
+    soa[Np + i] = hi[1];
+    soa[2 * Np + i] = hi[2];
+    soa[3 * Np + i] = m;
+    soa[4 * Np + i] = lo[0];
+    soa[5 * Np + i] = lo[1];
+    soa[6 * Np + i] = lo[2];
+}
 
 int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
                 cudaStream_t st);

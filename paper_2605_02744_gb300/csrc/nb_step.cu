@@ -1,8 +1,8 @@
 // O(N) kernels of the leapfrog step and the energy bookkeeping.
 //
 // kick_drift_pack: the opening half-kick and the drift of a kick-drift-kick
-// step, v += (dt/2) a; x += dt v, in FP64, followed by the FP32 SoA pack of
-// the new positions for the next force evaluation.  The closing half-kick is
+// step, v += (dt/2) a; x += dt v, in FP64, followed by the split FP32 SoA
+// pack (hi/lo) of the new positions for the next force evaluation.  The closing half-kick is
 // fused into the force kernel's epilogue.  This replaces the host-side FP64
 // predict/correct around the device evaluation of Sec. 2.1 / Sec. 3.1.
 //
@@ -23,7 +23,7 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ pos, double *__restr
     const double half = 0.5 * dt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float xs[3] = {0.f, 0.f, 0.f};
+        float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
         float m = 0.f;
         if (i < N) {
 #pragma unroll
@@ -32,14 +32,12 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ pos, double *__restr
                 const double x = pos[3 * i + c] + dt * v;
                 vel[3 * i + c] = v;
                 pos[3 * i + c] = x;
-                xs[c] = __double2float_rn(x);
+                hi[c] = __double2float_rn(x);
+                lo[c] = __double2float_rn(x - (double)hi[c]);
             }
             m = __double2float_rn(mass[i]);
         }
-        soa[i] = xs[0];
-        soa[Np + i] = xs[1];
-        soa[2 * Np + i] = xs[2];
-        soa[3 * Np + i] = m;
+        store_packed(soa, Np, i, hi, lo, m);
     }
 }
 
