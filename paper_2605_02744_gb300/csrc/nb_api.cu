@@ -104,6 +104,8 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     L.packA = off;
     off = align256(off + 4 * kPackArrays * (size_t)L.Np);
     L.packB = off;
+    off = align256(off + 16 * (size_t)L.Np);
+    L.cot64 = off;
     off = align256(off + 32 * (size_t)L.Np);
     L.records = off;
     off = align256(off + 2 * (size_t)L.max_grid * (size_t)L.record_bytes_per_i);

@@ -388,37 +388,49 @@ bool force_shape_compiled(const Shape &s) {
 }
 
 template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT>
-static int launch_sk(const ForceParams &p, int grid, cudaStream_t st) {
+static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
     auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT>;
     const size_t smem = (size_t)ST * (SPLIT ? 7 : 4) * 4 * TJ + (size_t)ST * 8;
+    static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
+    const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
 
 template <int NT, int IR, int TJ, int ST, int POL>
-static int launch_sk_gs(const ForceParams &p, bool guard, bool split, int grid, cudaStream_t st) {
+static int launch_sk_gs(const ForceParams &p, bool guard, bool split, int cps, cudaStream_t st) {
     if (guard)
-        return split ? launch_sk<NT, IR, TJ, ST, POL, true, true>(p, grid, st)
-                     : launch_sk<NT, IR, TJ, ST, POL, true, false>(p, grid, st);
-    return split ? launch_sk<NT, IR, TJ, ST, POL, false, true>(p, grid, st)
-                 : launch_sk<NT, IR, TJ, ST, POL, false, false>(p, grid, st);
+        return split ? launch_sk<NT, IR, TJ, ST, POL, true, true>(p, cps, st)
+                     : launch_sk<NT, IR, TJ, ST, POL, true, false>(p, cps, st);
+    return split ? launch_sk<NT, IR, TJ, ST, POL, false, true>(p, cps, st)
+                 : launch_sk<NT, IR, TJ, ST, POL, false, false>(p, cps, st);
 }
 
 template <int NT, int IR, int TJ, int ST>
-static int launch_sk_pol(const ForceParams &p, int pol, bool guard, bool split, int grid,
+static int launch_sk_pol(const ForceParams &p, int pol, bool guard, bool split, int cps,
                          cudaStream_t st) {
     switch (pol) {
-        case NB_PREC_FP32: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_FP32>(p, guard, split, grid, st);
-        case NB_PREC_KAHAN: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_KAHAN>(p, guard, split, grid, st);
-        case NB_PREC_F64ACC: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_F64ACC>(p, guard, split, grid, st);
+        case NB_PREC_FP32: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_FP32>(p, guard, split, cps, st);
+        case NB_PREC_KAHAN: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_KAHAN>(p, guard, split, cps, st);
+        case NB_PREC_F64ACC: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_F64ACC>(p, guard, split, cps, st);
     }
     return fail(NB_ERR_UNSUPPORTED, "precision %d has no FP32-pair kernel", pol);
 }
 
-int64_t force_grid(const Shape &sh, int64_t total) {
-    const int64_t slots = (int64_t)sh.ctas_per_sm * device_sm_count();
-    return std::max<int64_t>(1, std::min<int64_t>(slots, total));
+int occupancy(const void *kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+int persistent_grid(int cps, int occ, int64_t total) {
+    const int64_t per_sm = std::min(cps, occ);
+    const int64_t slots = per_sm * device_sm_count();
+    return (int)std::max<int64_t>(1, std::min<int64_t>(slots, total));
 }
 
 int launch_force(const ForceJob &j) {
@@ -460,10 +472,10 @@ int launch_force(const ForceJob &j) {
     p.counters = reinterpret_cast<uint32_t *>(j.ws + j.L.counters);
     p.status = status;
     p.timeout = j.timeout;
-    const int grid = (int)force_grid(sh, p.total);
 #define NB_DISPATCH(NT, IR, TJ, ST)                                                   \
     if (sh.threads == NT && sh.ipt == IR && sh.tile_j == TJ && sh.stages == ST)      \
-        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, j.split, grid, j.stream);
+        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, j.split, sh.ctas_per_sm, \
+                                             j.stream);
     NB_FORCE_SHAPES(NB_DISPATCH)
 #undef NB_DISPATCH
     return fail(NB_ERR_UNSUPPORTED, "force kernel shape (%d,%d,%d,%d) not compiled", sh.threads,

@@ -46,6 +46,10 @@ bool shape_compiled(const Shape &s, int kind);
 enum Kind { kKindForce = 0, kKindVjp = 1 };
 
 int device_sm_count();
+// Resident CTAs per SM of `kernel` (>= 1), and the persistent grid size:
+// min(requested CTAs per SM, occupancy) x SMs, capped at `total` items.
+int occupancy(const void *kernel, int threads, size_t smem);
+int persistent_grid(int cps, int occ, int64_t total);
 
 // --------------------------------------------------------- workspace
 // Byte offsets inside the caller's workspace.  Everything is 256-B aligned.
@@ -53,7 +57,8 @@ struct WsLayout {
     size_t status;    // uint32 status word (+ padding to 256 B)
     size_t counters;  // uint32 arrival counters, one per i-block
     size_t packA;     // float SoA [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
-    size_t packB;     // float SoA [8][Np]: VJP cotangent side
+    size_t packB;     // float SoA [4][Np]: VJP cotangents (cx, cy, cz, pbar/3)
+    size_t cot64;     // double SoA [4][Np]: the same cotangents in FP64
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
     size_t total;
