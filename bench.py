@@ -110,16 +110,30 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("nb_force.cu", "nb_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_02744_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic():
-    """DRAM bytes per force launch from the committed ncu summary, or None."""
+    """DRAM bytes per force launch from the committed ncu summary, or None
+    when the kernel source changed after the counters were taken."""
+    vals = {}
     try:
         with open(TRAFFIC_FILE) as f:
             for line in f:
-                if line.startswith("dram_bytes_per_launch:"):
-                    return float(line.split(":")[1])
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
     except OSError:
-        pass
-    return None
+        return None
+    if vals.get("source_sha256_16") != _kernel_source_hash():
+        return None
+    return float(vals["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in vals else None
 
 
 def cpu_baseline(seconds: float = 10.0):
@@ -346,6 +360,24 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A few nb_forces calls at --profile N (Kahan, split positions): the
+    small and full-size cases the ncu captures under profiles/ were taken on."""
+    import torch
+
+    import paper_2605_02744_gb300 as pkg
+    from paper_2605_02744_gb300 import api, ics
+    pkg.build()
+    n = int(args.profile)
+    s = ics.plummer(n, seed=0)
+    pos = torch.tensor(s.pos, device="cuda")
+    mass = torch.tensor(s.mass, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        api.forces(pos, mass, EPS_MAIN, precision=args.precision)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,10 +387,15 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="run only nb_forces on a Plummer sphere of this size (for ncu)")
+    ap.add_argument("--precision", default="kahan")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile_case(args)
     return run_ours(args)
 
 
