@@ -137,6 +137,29 @@ int nb_forces(const double *pos, const double *mass, int64_t N, double eps, doub
               double *pot, void *ws, size_t ws_bytes, const nb_opts *opts);
 
 /*
+ * nb_forces for callers that cannot allocate device memory and therefore
+ * cannot hand the library a workspace: for instance a plug-in whose host
+ * application owns every device allocation through its own pool, or a
+ * latency-critical loop that must never reach cudaMalloc (it can block and
+ * synchronise the device).  The paper has no counterpart; this is a
+ * convenience of this library.
+ *
+ * Same arguments and results as nb_forces without (ws, ws_bytes): the
+ * scratch is a fixed device array inside the library (about 6.2 MB, held on
+ * every GPU that loads the library until the process exits), so N is limited
+ * to 32768; larger N returns NB_ERR_INVALID.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on each device before capturing any CUDA stream.  Every call
+ * shares the one array: calls that may overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  Each call clears the array's counters and status word itself.
+ * Device-side errors (a non-finite result, a wait that ran out) are not
+ * reported by this variant; host-side argument errors are.
+ */
+int nb_forces_noalloc(const double *pos, const double *mass, int64_t N, double eps, double *acc,
+                      double *pot, const nb_opts *opts);
+
+/*
  * Accelerations and potentials of B independent clusters in one launch; the
  * particles of cluster c are offsets[c] .. offsets[c+1]-1 and interact only
  * with each other.  offsets (int64 [B+1]) and eps (double [B]) are device

@@ -36,7 +36,8 @@ POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_
 
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
-            "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status")
+            "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
+            "nb_forces_noalloc")
 
 
 class NbError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "nb_step_vjp_reverse": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _d, _d, _d, _d, _d, _vp, _vp,
                                            _vp, _vp, _sz, _OPTS]),
     "nb_poll_status": (ctypes.c_int, [_vp, _sz, _vp]),
+    "nb_forces_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _OPTS]),
 }
 
 
@@ -188,6 +190,17 @@ def nb_forces(pos, mass, eps: float, acc, pot, ws, opts: nb_opts):
     _check(lib().nb_forces(_dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n, float(eps),
                            _dptr(acc, "acc", f64), _dptr(pot, "pot", f64, True),
                            _dptr(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_forces_noalloc(pos, mass, eps: float, acc, pot, opts: nb_opts):
+    """nb_forces without a workspace, for callers that may not allocate
+    device memory (N <= 32768; scratch is a fixed array in the library)."""
+    import torch
+    f64 = torch.float64
+    n = mass.shape[0]
+    _check(lib().nb_forces_noalloc(_dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n,
+                                   float(eps), _dptr(acc, "acc", f64),
+                                   _dptr(pot, "pot", f64, True), ctypes.byref(opts)))
 
 
 def nb_forces_batched(pos, mass, offsets, eps, acc, pot, ws, opts: nb_opts):
