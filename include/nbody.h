@@ -88,6 +88,7 @@ typedef struct nb_tune {
     int32_t tile_j;       /* j-particles per shared-memory stage: 64..512   */
     int32_t stages;       /* depth of the bulk-copy ring: 2..4               */
     int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..4                    */
+    int32_t cluster_ctas; /* batched kernel: CTAs per thread-block cluster, 2/4/8 */
 } nb_tune;
 
 typedef struct nb_opts {
@@ -162,14 +163,19 @@ int nb_forces_noalloc(const double *pos, const double *mass, int64_t N, double e
 /*
  * Accelerations and potentials of B independent clusters in one launch; the
  * particles of cluster c are offsets[c] .. offsets[c+1]-1 and interact only
- * with each other.  offsets (int64 [B+1]) and eps (double [B]) are device
- * arrays; each cluster must hold between 1 and 8192 particles, and every
- * eps[c] must be > 0.  Other arguments as nb_forces.  The work division over
- * clusters follows the SPMD split of Sec. 3.1 (independent work per core).
+ * with each other.  offsets (int64 [B+1], offsets[0] = 0, offsets[B] = N) and
+ * eps (double [B]) are device arrays; each cluster must hold between 1 and
+ * 8192 particles and every eps[c] must be > 0.  These device-side
+ * conditions are checked on the device: a violating cluster is skipped and
+ * NB_ERR_INVALID is latched for nb_poll_status.  N is the total particle
+ * count (the workspace is sized with nb_workspace_bytes(N, B, opts)).  FP32
+ * pairs only (precision FP32, KAHAN or F64ACC; positions always split).
+ * The work division over clusters follows the SPMD split of Sec. 3.1
+ * (independent work per core), one system per thread-block cluster.
  */
 int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
-                      const double *eps, double *acc, double *pot, void *ws, size_t ws_bytes,
-                      const nb_opts *opts);
+                      int64_t N, const double *eps, double *acc, double *pot, void *ws,
+                      size_t ws_bytes, const nb_opts *opts);
 
 /*
  * State advanced by nb_step.  Single system: B = 1, offsets = NULL, eps used.

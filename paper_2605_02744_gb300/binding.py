@@ -53,7 +53,7 @@ class NbLibraryMissing(RuntimeError):
 class nb_tune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("i_per_thread", ctypes.c_int32),
                 ("tile_j", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32)]
 
 
 class nb_opts(ctypes.Structure):
@@ -86,7 +86,8 @@ _SIGS = {
     "nb_tune_valid": (ctypes.c_int, [ctypes.POINTER(nb_tune)]),
     "nb_workspace_bytes": (_sz, [_i64, _i32, _OPTS]),
     "nb_forces": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _sz, _OPTS]),
-    "nb_forces_batched": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _OPTS]),
+    "nb_forces_batched": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _vp, _vp, _sz,
+                                         _OPTS]),
     "nb_step": (ctypes.c_int, [_STATE, _d, _i64, _OPTS]),
     "nb_energy": (ctypes.c_int, [_STATE, _vp, _OPTS]),
     "nb_forces_vjp": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _vp, _sz, _OPTS]),
@@ -209,7 +210,7 @@ def nb_forces_batched(pos, mass, offsets, eps, acc, pot, ws, opts: nb_opts):
     B = offsets.shape[0] - 1
     _check(lib().nb_forces_batched(
         _dptr(pos, "pos", f64), _dptr(mass, "mass", f64), _dptr(offsets, "offsets", torch.int64),
-        B, _dptr(eps, "eps", f64), _dptr(acc, "acc", f64), _dptr(pot, "pot", f64, True),
+        B, mass.shape[0], _dptr(eps, "eps", f64), _dptr(acc, "acc", f64), _dptr(pot, "pot", f64, True),
         _dptr(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(opts)))
 
 

@@ -257,11 +257,13 @@ int nb_forces(const double *pos, const double *mass, int64_t N, double eps, doub
 }
 
 int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
-                      const double *eps, double *acc, double *pot, void *ws, size_t ws_bytes,
-                      const nb_opts *o) {
+                      int64_t N, const double *eps, double *acc, double *pot, void *ws,
+                      size_t ws_bytes, const nb_opts *o) {
     clear_error();
     if (!o) return fail(NB_ERR_INVALID, "opts is NULL");
     if (B < 1) return fail(NB_ERR_INVALID, "B must be >= 1");
+    if (N < B) return fail(NB_ERR_INVALID, "N must be >= B (every cluster holds a particle)");
+    if (N > (int64_t)1 << 30) return fail(NB_ERR_INVALID, "N above 2^30 is not supported");
     NB_TRY(check_ptr(pos, "pos"));
     NB_TRY(check_ptr(mass, "mass"));
     NB_TRY(check_ptr(offsets, "offsets"));
@@ -271,12 +273,9 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     if (!isfinite(o->G)) return fail(NB_ERR_INVALID, "G must be finite");
     if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
         return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
-    // N_total is only known on the device; the caller's workspace must have
-    // been sized with the same B and an N_total that bounds offsets[B].
     BatchedJob j{};
-    j.L = ws_layout(1, B, o);
-    if (!ws || ((uintptr_t)ws & 255)) return fail(NB_ERR_INVALID, "workspace NULL or misaligned");
-    if (ws_bytes < j.L.total) return fail(NB_ERR_WORKSPACE, "workspace too small for B=%d", B);
+    j.L = ws_layout(N, B, o);
+    NB_TRY(check_ws(ws, ws_bytes, j.L));
     j.mass = mass;
     j.offsets = offsets;
     j.B = B;
@@ -286,14 +285,40 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.vel = nullptr;
     j.acc = acc;
     j.pot = pot;
-    j.N = -1;
+    j.N = N;
     j.dt = 0.0;
     j.nsteps = 0;
     j.acc_valid = false;
     j.precision = o->precision;
+    j.cluster = o->tune ? o->tune->cluster_ctas : 0;
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)ws;
+    return launch_batched(j);
+}
+
+static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
+    BatchedJob j{};
+    j.L = ws_layout(s->N, s->B, o);
+    NB_TRY(check_ws(s->ws, s->ws_bytes, j.L));
+    j.mass = s->mass;
+    j.offsets = s->offsets;
+    j.B = s->B;
+    j.eps = s->eps_b;
+    j.G = o->G;
+    j.pos = s->pos;
+    j.vel = s->vel;
+    j.acc = s->acc;
+    j.pot = s->pot;
+    j.N = s->N;
+    j.dt = dt;
+    j.nsteps = nsteps;
+    j.acc_valid = s->acc_valid != 0;
+    j.precision = o->precision;
+    j.cluster = o->tune ? o->tune->cluster_ctas : 0;
+    j.timeout = timeout_of(o);
+    j.stream = (cudaStream_t)o->stream;
+    j.ws = (char *)s->ws;
     return launch_batched(j);
 }
 
@@ -325,40 +350,24 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
     NB_TRY(check_ptr(s->mass, "state.mass"));
     NB_TRY(check_ptr(s->acc, "state.acc"));
     NB_TRY(check_ptr(s->pot, "state.pot", true));
-    if (s->B > 1 || s->offsets) {
+    const bool batched = s->B > 1 || s->offsets;
+    if (batched) {
         if (s->B < 1) return fail(NB_ERR_INVALID, "B must be >= 1");
         NB_TRY(check_ptr(s->offsets, "state.offsets"));
         NB_TRY(check_ptr(s->eps_b, "state.eps_b"));
-        if (s->N < 1) return fail(NB_ERR_INVALID, "N must be >= 1");
-        BatchedJob j{};
-        j.L = ws_layout(s->N, s->B, o);
-        NB_TRY(check_ws(s->ws, s->ws_bytes, j.L));
-        j.mass = s->mass;
-        j.offsets = s->offsets;
-        j.B = s->B;
-        j.eps = s->eps_b;
-        j.G = o->G;
-        j.pos = s->pos;
-        j.vel = s->vel;
-        j.acc = s->acc;
-        j.pot = s->pot;
-        j.N = s->N;
-        j.dt = dt;
-        j.nsteps = nsteps;
-        j.acc_valid = s->acc_valid != 0;
-        j.precision = o->precision;
-        j.timeout = timeout_of(o);
-        j.stream = (cudaStream_t)o->stream;
-        j.ws = (char *)s->ws;
-        NB_TRY(launch_batched(j));
-        s->acc_valid = 1;
-        s->step += nsteps;
-        return NB_OK;
+        if (s->N < s->B) return fail(NB_ERR_INVALID, "N must be >= B");
+        if (!isfinite(o->G)) return fail(NB_ERR_INVALID, "G must be finite");
+        if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
+            return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
+    } else {
+        NB_TRY(check_common(o, s->N, s->eps));
     }
-    NB_TRY(check_common(o, s->N, s->eps));
+    auto run = [&]() {
+        return batched ? step_batched_direct(s, dt, nsteps, o) : step_single_direct(s, dt, nsteps, o);
+    };
     const bool graph = o->use_graph && o->stream != nullptr && nsteps > 0;
     if (!graph) {
-        NB_TRY(step_single_direct(s, dt, nsteps, o));
+        NB_TRY(run());
     } else {
         GraphKey key;
         memset(&key, 0, sizeof key);
@@ -389,6 +398,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
             key.t.tile_j = o->tune->tile_j;
             key.t.stages = o->tune->stages;
             key.t.ctas_per_sm = o->tune->ctas_per_sm;
+            key.t.cluster_ctas = o->tune->cluster_ctas;
         }
         cudaGetDevice(&key.device);
         cudaGraphExec_t exec = nullptr;
@@ -402,7 +412,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
             // The first call of a new configuration captures the loop (state
             // pointers, sizes and dt are baked into the graph).
             NB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            const int rc = step_single_direct(s, dt, nsteps, o);
+            const int rc = run();
             cudaGraph_t g = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (rc != NB_OK) {

@@ -90,6 +90,45 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// ------------------------------------------------------------ pair loop
+// Two j-particles (packed in the .x/.y halves) against IR i-particles.
+// The displacement is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) when SPLIT.
+template <int IR, bool GUARD, bool SPLIT>
+__device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const float2 zj,
+                                      const float2 xl, const float2 yl, const float2 zl,
+                                      const float2 mj, const float2 eps2, const float2 (&nx)[IR],
+                                      const float2 (&ny)[IR], const float2 (&nz)[IR],
+                                      const float2 (&nxl)[IR], const float2 (&nyl)[IR],
+                                      const float2 (&nzl)[IR], float2 (&ax)[IR],
+                                      float2 (&ay)[IR], float2 (&az)[IR], float2 (&ph)[IR]) {
+#pragma unroll
+    for (int k = 0; k < IR; ++k) {
+        float2 dx = add2(xj, nx[k]);
+        float2 dy = add2(yj, ny[k]);
+        float2 dz = add2(zj, nz[k]);
+        if (SPLIT) {
+            dx = add2(dx, add2(xl, nxl[k]));
+            dy = add2(dy, add2(yl, nyl[k]));
+            dz = add2(dz, add2(zl, nzl[k]));
+        }
+        float2 r2 = fma2(dx, dx, eps2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        if (GUARD) {
+            ri.x = r2.x > 0.f ? ri.x : 0.f;
+            ri.y = r2.y > 0.f ? ri.y : 0.f;
+        }
+        const float2 s = mul2(mj, ri);
+        const float2 ri2 = mul2(ri, ri);
+        const float2 s3 = mul2(s, ri2);
+        ax[k] = fma2(s3, dx, ax[k]);
+        ay[k] = fma2(s3, dy, ay[k]);
+        az[k] = fma2(s3, dz, az[k]);
+        ph[k] = add2(ph[k], s);
+    }
+}
+
 // --------------------------------------------------- accumulation policies
 // Per-particle running sums across j-tiles.  Each tile's FP32 partial is
 // folded in once per tile.

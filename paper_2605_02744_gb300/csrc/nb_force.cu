@@ -26,6 +26,7 @@ namespace nb {
 
 using dev::Acc;
 using dev::Record;
+using dev::pair2;
 
 // ------------------------------------------------------------------ pack
 // FP64 [N][3] positions + [N] masses -> float SoA of 7 arrays of Np:
@@ -79,45 +80,6 @@ struct ForceParams {
     uint32_t *status;
     long long timeout;
 };
-
-// Two j-particles (packed in the .x/.y halves) against IR i-particles.
-// The displacement is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) when SPLIT.
-template <int IR, bool GUARD, bool SPLIT>
-__device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const float2 zj,
-                                      const float2 xl, const float2 yl, const float2 zl,
-                                      const float2 mj, const float2 eps2, const float2 (&nx)[IR],
-                                      const float2 (&ny)[IR], const float2 (&nz)[IR],
-                                      const float2 (&nxl)[IR], const float2 (&nyl)[IR],
-                                      const float2 (&nzl)[IR], float2 (&ax)[IR],
-                                      float2 (&ay)[IR], float2 (&az)[IR], float2 (&ph)[IR]) {
-    using namespace dev;
-#pragma unroll
-    for (int k = 0; k < IR; ++k) {
-        float2 dx = add2(xj, nx[k]);
-        float2 dy = add2(yj, ny[k]);
-        float2 dz = add2(zj, nz[k]);
-        if (SPLIT) {
-            dx = add2(dx, add2(xl, nxl[k]));
-            dy = add2(dy, add2(yl, nyl[k]));
-            dz = add2(dz, add2(zl, nzl[k]));
-        }
-        float2 r2 = fma2(dx, dx, eps2);
-        r2 = fma2(dy, dy, r2);
-        r2 = fma2(dz, dz, r2);
-        float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        if (GUARD) {
-            ri.x = r2.x > 0.f ? ri.x : 0.f;
-            ri.y = r2.y > 0.f ? ri.y : 0.f;
-        }
-        const float2 s = mul2(mj, ri);
-        const float2 ri2 = mul2(ri, ri);
-        const float2 s3 = mul2(s, ri2);
-        ax[k] = fma2(s3, dx, ax[k]);
-        ay[k] = fma2(s3, dy, ay[k]);
-        az[k] = fma2(s3, dz, az[k]);
-        ph[k] = add2(ph[k], s);
-    }
-}
 
 template <int NT, int IR, int POL, bool GUARD>
 __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,

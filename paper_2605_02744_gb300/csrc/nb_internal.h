@@ -178,6 +178,7 @@ struct BatchedJob {
     int64_t nsteps;   // 0 = forces only
     bool acc_valid;
     int precision;
+    int cluster;      // CTAs per thread-block cluster (0 = default)
     long long timeout;
     cudaStream_t stream;
     char *ws;

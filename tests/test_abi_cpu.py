@@ -124,7 +124,9 @@ def test_step_and_vjp_argument_checks(B):
                            ctypes.byref(o)) == 1
     assert lib.nb_step_vjp(FAKE, FAKE, 16, 0.1, 1e-3, 5e-4, FAKE, None, FAKE, FAKE, wsb,
                            ctypes.byref(o)) == 1
-    assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 0, FAKE, FAKE, None, FAKE, 1 << 30,
+    assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 0, 16, FAKE, FAKE, None, FAKE, 1 << 30,
+                                 ctypes.byref(o)) == 1
+    assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 4, 3, FAKE, FAKE, None, FAKE, 1 << 30,
                                  ctypes.byref(o)) == 1
     assert lib.nb_energy(ctypes.byref(st), None, ctypes.byref(o)) == 1
     assert lib.nb_poll_status(None, 0, None) == 1
