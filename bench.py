@@ -212,6 +212,68 @@ def _time_steps(system, dt, steps, flush, torch):
     return times
 
 
+def batched_rate(torch, steps=1000):
+    """512 independent Plummer clusters (N_c log-uniform 64..8192, eps 0.01),
+    `steps` KDK steps dt=1e-3 in one persistent launch replayed as a CUDA
+    graph, cluster size from the autotuner."""
+    import numpy as np
+
+    from paper_2605_02744_gb300 import api, ics, tune
+    s = ics.batched_plummer(512, seed=1)
+    sizes = np.diff(s.offsets).astype(np.float64)
+    eps = np.full(512, 0.01)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        best = tune.autotune_batched(torch.tensor(s.pos, device="cuda"),
+                                     torch.tensor(s.vel, device="cuda"),
+                                     torch.tensor(s.mass, device="cuda"), s.offsets, eps, 1e-3,
+                                     nsteps=20, reps=2, store=False)
+        g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc",
+                       tune=best, stream=st, use_graph=True)
+        g.forces()
+        g.step(1e-3, steps)  # first call captures the step loop as a graph
+        g.pos.copy_(torch.tensor(s.pos, device="cuda"))
+        g.vel.copy_(torch.tensor(s.vel, device="cuda"))
+        g.forces()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(1e-3, steps)  # graph replay
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ok = g.poll()
+    inter = float((sizes ** 2).sum()) * steps
+    return {"workload": f"512 Plummer clusters, N_c log-uniform [64, 8192] (seed 1), "
+                        f"eps=0.01, {steps} KDK steps dt=1e-3, F64ACC, one persistent launch "
+                        f"in a CUDA graph", "tune": best, "ms": ms,
+            "value": inter / (ms * 1e-3) / 1e9, "unit": UNIT, "status": ok,
+            "interactions": inter}
+
+
+def variant_rates(torch):
+    """One force+potential at the 65536-particle log-normal workload per variant."""
+    from paper_2605_02744_gb300 import api, ics
+    s = ics.plummer_lognormal(65536, seed=0)
+    pos = torch.tensor(s.pos, device="cuda")
+    mass = torch.tensor(s.mass, device="cuda")
+    out = {}
+    for prec, pos_mode in (("f64acc", "default"), ("kahan", "default"), ("fp32", "default"),
+                           ("fp64", "default")):
+        reps = 2 if prec == "fp64" else 10
+        api.forces(pos, mass, 1e-3, precision=prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            api.forces(pos, mass, 1e-3, precision=prec)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[prec] = {"ms": ms, "value": 65536.0 ** 2 / (ms * 1e-3) / 1e9}
+    return out
+
+
 def adjoint_ratio(torch):
     """Forward (200 KDK steps) vs gradient time at the 16384-particle workload."""
     from paper_2605_02744_gb300 import adjoint, ics
@@ -301,12 +363,21 @@ def run_ours(args):
     d2h = sum(v.numel() * 8 for v in outs.values()) + 24
     del e2e_sys
 
-    adj = None
+    adj = batched = variants = None
     if not args.skip_adjoint:
         try:
             adj = adjoint_ratio(torch)
         except Exception as e:  # reported, never silently replaced
             adj = {"error": f"{type(e).__name__}: {e}"}
+    if not args.skip_extra:
+        try:
+            batched = batched_rate(torch)
+        except Exception as e:
+            batched = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            variants = variant_rates(torch)
+        except Exception as e:
+            variants = {"error": f"{type(e).__name__}: {e}"}
 
     if rank != 0:
         if ws > 1:
@@ -349,8 +420,10 @@ def run_ours(args):
         "gpu_launches": 4 * args.steps,
         "variants": {"f64acc_value": ws * args.steps * inter / (sum(results["f64acc"][0]) * 1e-3)
                      / 1e9, "f64acc_ms_per_step": f64_ms,
-                     "kahan_ms_per_step": step_ms},
+                     "kahan_ms_per_step": step_ms,
+                     "lognormal_65536_per_precision": variants},
         "adjoint": adj,
+        "batched": batched,
     }
     if ws == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -386,6 +459,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the batched and per-precision side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--profile", type=int, default=0,
                     help="run only nb_forces on a Plummer sphere of this size (for ncu)")

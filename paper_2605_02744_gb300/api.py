@@ -14,9 +14,25 @@ def _dev_f64(x, device):
     return torch.as_tensor(x, dtype=torch.float64).to(device).contiguous()
 
 
+def _resolve_tune(tune, kind, precision, n, autotune):
+    """tune="auto": the cached choice for this device and size, tuned on a miss."""
+    if tune != "auto":
+        return tune
+    from . import tune as T
+    hit = T.lookup(kind, precision, n)
+    return hit if hit is not None else autotune()
+
+
 def forces(pos, mass, eps: float, precision="f64acc", G: float = 1.0, with_pot: bool = True,
            tune=None, ws=None, stream=None):
-    """(acc, pot) for one system; pos [N,3], mass [N] CUDA float64 tensors."""
+    """(acc, pot) for one system; pos [N,3], mass [N] CUDA float64 tensors.
+
+    tune: None (built-in shapes), an nb_tune dict, or "auto" (autotuner cache).
+    """
+    if tune == "auto":
+        from . import tune as T
+        tune = _resolve_tune(tune, "force", precision, mass.shape[0],
+                             lambda: T.autotune_forces(pos, mass, eps, precision))
     opts = B.make_opts(precision, G, stream, tune=tune)
     n = mass.shape[0]
     acc = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
@@ -74,6 +90,17 @@ class System:
         self.vel = _dev_f64(vel, self.device)
         self.mass = _dev_f64(mass, self.device)
         n = self.mass.shape[0]
+        if tune == "auto":
+            from . import tune as T
+            if offsets is None:
+                tune = _resolve_tune(tune, "force", precision, n,
+                                     lambda: T.autotune_forces(self.pos, self.mass, eps,
+                                                               precision))
+            else:
+                tune = _resolve_tune(tune, "batched", precision, n,
+                                     lambda: T.autotune_batched(self.pos, self.vel, self.mass,
+                                                                offsets, eps, 1e-3,
+                                                                precision=precision))
         self.acc = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
         self.pot = torch.zeros(n, dtype=torch.float64, device=self.device)
         self.opts = B.make_opts(precision, G, stream, use_graph=use_graph, tune=tune)

@@ -50,11 +50,15 @@ bool shape_compiled(const Shape &s, int kind) {
     return kind == kKindForce ? force_shape_compiled(s) : vjp_shape_compiled(s);
 }
 
+// Built-in shapes, from an autotuner sweep on GB300 (Kahan / F64ACC, split
+// positions): (256 threads, 4 i/thread, 256-j tiles, 3 stages) is fastest
+// from N = 65536 up; (256, 2, 256, 3) at N = 16384; (128, 1, 64, 2) at 1024.
+// CTAs per SM are clamped by register occupancy (one 256-thread CTA).
 Shape default_shape(int64_t N, int precision, int kind) {
     (void)precision;
     if (kind == kKindForce) {
-        if (N >= (1 << 17)) return Shape{256, 4, 256, 3, 2};
-        if (N >= (1 << 13)) return Shape{128, 2, 128, 3, 4};
+        if (N >= (1 << 15)) return Shape{256, 4, 256, 3, 2};
+        if (N >= (1 << 12)) return Shape{256, 2, 256, 3, 2};
         return Shape{128, 1, 64, 2, 4};
     }
     if (N >= (1 << 15)) return Shape{128, 2, 128, 3, 4};
