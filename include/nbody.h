@@ -74,9 +74,14 @@ typedef enum {
  * (Sec. 3.1); its displacement error is ~6e-8 |x| / |x_j - x_i|, which
  * reaches ~1e-4 relative acceleration error for close pairs at N = 2^20. */
 typedef enum {
-    NB_POS_DEFAULT = 0, /* SPLIT for KAHAN and F64ACC, SINGLE for FP32      */
+    NB_POS_DEFAULT = 0, /* KAHAN/F64ACC: SPLIT below N = 262144, ADAPTIVE
+                           from there; FP32: SINGLE                        */
     NB_POS_SPLIT = 1,
-    NB_POS_SINGLE = 2
+    NB_POS_SINGLE = 2,
+    NB_POS_ADAPTIVE = 3 /* particles sorted along a Morton curve each call;
+                           SPLIT for tile pairs whose bounding boxes are
+                           closer than near_gamma (default 1/64) times
+                           their largest coordinate, SINGLE for the rest   */
 } nb_positions;
 
 /* Launch shape of the FP32-pair kernels.  Zero fields take the built-in
@@ -100,6 +105,9 @@ typedef struct nb_opts {
     int64_t timeout_cycles; /* bound on every device wait, in SM clock cycles;
                                0 = default (about 2 s)                         */
     int32_t positions;      /* nb_positions (ignored by NB_PREC_FP64)          */
+    float near_gamma;       /* NB_POS_ADAPTIVE: a tile pair is well separated
+                               when its box gap >= near_gamma x the largest
+                               coordinate magnitude; 0 = default (1/64)     */
 } nb_opts;
 
 /* Fills *opts with precision F64ACC, G = 1, default stream, no graph,

@@ -32,7 +32,9 @@ PRECISIONS = {"fp32": NB_PREC_FP32, "kahan": NB_PREC_KAHAN, "f64acc": NB_PREC_F6
 NB_POS_DEFAULT = 0
 NB_POS_SPLIT = 1
 NB_POS_SINGLE = 2
-POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_SINGLE}
+NB_POS_ADAPTIVE = 3
+POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_SINGLE,
+             "adaptive": NB_POS_ADAPTIVE}
 
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
@@ -60,7 +62,7 @@ class nb_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("G", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32),
                 ("tune", ctypes.POINTER(nb_tune)), ("timeout_cycles", ctypes.c_int64),
-                ("positions", ctypes.c_int32)]
+                ("positions", ctypes.c_int32), ("near_gamma", ctypes.c_float)]
 
 
 class nb_state(ctypes.Structure):
@@ -138,7 +140,8 @@ def _dptr(t, name, dtype=None, optional=False):
 
 
 def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool = False,
-              tune=None, timeout_cycles: int = 0, positions="default") -> nb_opts:
+              tune=None, timeout_cycles: int = 0, positions="default",
+              near_gamma: float = 0.0) -> nb_opts:
     """nb_opts for a call; stream None = torch's current stream on the current device."""
     o = nb_opts()
     lib().nb_opts_default(ctypes.byref(o))
@@ -156,6 +159,7 @@ def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool =
         o.tune = ctypes.pointer(tune)
     o.timeout_cycles = int(timeout_cycles)
     o.positions = POSITIONS[positions] if isinstance(positions, str) else int(positions)
+    o.near_gamma = float(near_gamma)
     return o
 
 

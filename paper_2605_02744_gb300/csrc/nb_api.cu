@@ -111,6 +111,8 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     off = align256(off + 16 * (size_t)L.Np);
     L.cot64 = off;
     off = align256(off + 32 * (size_t)L.Np);
+    L.sortbuf = off;
+    off = align256(off + sortbuf_bytes(L.Np));
     L.records = off;
     off = align256(off + 2 * (size_t)L.max_grid * (size_t)L.record_bytes_per_i);
     L.scratch = off;
@@ -129,9 +131,18 @@ int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L) {
 }
 
 bool positions_split(const nb_opts *o) {
-    if (o->positions == NB_POS_SPLIT) return true;
+    if (o->positions == NB_POS_SPLIT || o->positions == NB_POS_ADAPTIVE) return true;
     if (o->positions == NB_POS_SINGLE) return false;
     return o->precision != NB_PREC_FP32;
+}
+
+constexpr int64_t kAdaptiveMinN = 1 << 18;  // below, the sort costs more than it saves
+
+bool positions_adaptive(const nb_opts *o, int64_t N) {
+    if (o->precision == NB_PREC_FP64) return false;
+    if (o->positions == NB_POS_ADAPTIVE) return true;
+    if (o->positions != NB_POS_DEFAULT) return false;
+    return o->precision != NB_PREC_FP32 && N >= kAdaptiveMinN;
 }
 
 // ------------------------------------------------------------ checks
@@ -152,8 +163,10 @@ static int check_common(const nb_opts *o, int64_t N, double eps) {
     if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
         return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
     if (o->timeout_cycles < 0) return fail(NB_ERR_INVALID, "timeout_cycles must be >= 0");
-    if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_SINGLE)
+    if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_ADAPTIVE)
         return fail(NB_ERR_INVALID, "unknown positions mode %d", o->positions);
+    if (!(o->near_gamma >= 0.f) || !isfinite(o->near_gamma))
+        return fail(NB_ERR_INVALID, "near_gamma must be finite and >= 0");
     return NB_OK;
 }
 
@@ -190,6 +203,8 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     j->kick = 0.0;
     j->precision = o->precision;
     j->split = positions_split(o);
+    j->adaptive = positions_adaptive(o, N);
+    j->gamma = o->near_gamma > 0.f ? o->near_gamma : kNearFarGamma;
     j->packed_ready = false;
     j->timeout = timeout_of(o);
     j->stream = (cudaStream_t)o->stream;
@@ -332,10 +347,11 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
     if (!s->acc_valid) NB_TRY(launch_force(j));
     float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
     for (int64_t n = 0; n < nsteps; ++n) {
-        NB_TRY(launch_kick_drift_pack(s->pos, s->vel, s->acc, s->mass, s->N, j.L.Np, dt, soa,
-                                      j.stream));
+        // the adaptive path packs in Morton order inside launch_force
+        NB_TRY(launch_kick_drift_pack(s->pos, s->vel, s->acc, s->mass, s->N, j.L.Np, dt,
+                                      j.adaptive ? nullptr : soa, j.stream));
         ForceJob k = j;
-        k.packed_ready = true;
+        k.packed_ready = !j.adaptive;
         k.vel = s->vel;
         k.kick = 0.5 * dt;
         NB_TRY(launch_force(k));
@@ -396,6 +412,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
         key.o.use_graph = o->use_graph;
         key.o.timeout_cycles = o->timeout_cycles;
         key.o.positions = o->positions;
+        key.o.near_gamma = o->near_gamma;
         if (o->tune) {
             key.t.threads = o->tune->threads;
             key.t.i_per_thread = o->tune->i_per_thread;

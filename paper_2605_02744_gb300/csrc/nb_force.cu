@@ -79,17 +79,33 @@ struct ForceParams {
     uint32_t *counters;
     uint32_t *status;
     long long timeout;
+    // adaptive displacement (NF): particles packed in Morton order
+    const float *tile_box;   // [N/64][8]: lo[3] hi[3] max|x| pad, per 64 j-slots
+    const float *block_box;  // [N/(32 IR)][8], per warp's 32 IR i-slots
+    const int *perm;         // packed slot -> particle index
+    float gamma;             // far iff box gap >= gamma * max|x|
 };
 
-template <int NT, int IR, int POL, bool GUARD>
+// Packed slot of register row k of thread tid in i-block b.  The adaptive
+// path (NF) gives each warp 32*IR contiguous slots, so a warp's particles
+// share one small box in the Morton-sorted pack; otherwise rows are strided
+// by the CTA width (coalesced loads and stores).
+template <int NT, int IR, bool NF>
+__device__ __forceinline__ int64_t slot_of(int64_t b, int k, int tid) {
+    if (NF) return b * NT * IR + (int64_t)(tid >> 5) * 32 * IR + k * 32 + (tid & 31);
+    return b * NT * IR + k * NT + tid;
+}
+
+template <int NT, int IR, int POL, bool GUARD, bool NF>
 __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
                                                const Acc<POL> (&acc)[IR][4], const float (&mi)[IR]) {
     constexpr int BI = NT * IR;
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
-        const int64_t i = b * BI + k * NT + threadIdx.x;
-        if (i < p.N) {
+        const int64_t slot = slot_of<NT, IR, NF>(b, k, threadIdx.x);
+        if (slot < p.N) {
+            const int64_t i = NF ? (int64_t)p.perm[slot] : slot;
             double phs = acc[k][3].value();
             if (!GUARD) phs -= (double)(mi[k] * dev::rsqrt_approx(p.eps2));  // self pair
             const double gx = p.G * acc[k][0].value();
@@ -111,7 +127,55 @@ __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
     if (bad) dev::set_status(p.status, kStatusNonFinite);
 }
 
-template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT>
+// Staged j-particles [j0, j1) of one tile against the thread's IR
+// i-particles (two j per packed instruction); SPLIT picks the hi/lo
+// displacement.
+template <int IR, int TJ, bool GUARD, bool SPLIT>
+__device__ __forceinline__ void tile_pairs(const float *sx, const int j0, const int j1,
+                                           const float2 eps2,
+                                           const float2 (&nx)[IR], const float2 (&ny)[IR],
+                                           const float2 (&nz)[IR], const float2 (&nxl)[IR],
+                                           const float2 (&nyl)[IR], const float2 (&nzl)[IR],
+                                           float2 (&ax)[IR], float2 (&ay)[IR], float2 (&az)[IR],
+                                           float2 (&ph)[IR]) {
+    using dev::f2;
+    const float *sy = sx + TJ, *sz = sx + 2 * TJ, *sm = sx + 3 * TJ;
+    const float *sxl = sx + 4 * TJ, *syl = sx + 5 * TJ, *szl = sx + 6 * TJ;
+#pragma unroll 2
+    for (int jj = j0; jj < j1; jj += 4) {
+        const float4 X = *reinterpret_cast<const float4 *>(sx + jj);
+        const float4 Y = *reinterpret_cast<const float4 *>(sy + jj);
+        const float4 Z = *reinterpret_cast<const float4 *>(sz + jj);
+        const float4 M = *reinterpret_cast<const float4 *>(sm + jj);
+        float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
+        if (SPLIT) {
+            XL = *reinterpret_cast<const float4 *>(sxl + jj);
+            YL = *reinterpret_cast<const float4 *>(syl + jj);
+            ZL = *reinterpret_cast<const float4 *>(szl + jj);
+        }
+        pair2<IR, GUARD, SPLIT>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(XL.x, XL.y),
+                                f2(YL.x, YL.y), f2(ZL.x, ZL.y), f2(M.x, M.y), eps2, nx, ny, nz,
+                                nxl, nyl, nzl, ax, ay, az, ph);
+        pair2<IR, GUARD, SPLIT>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(XL.z, XL.w),
+                                f2(YL.z, YL.w), f2(ZL.z, ZL.w), f2(M.z, M.w), eps2, nx, ny, nz,
+                                nxl, nyl, nzl, ax, ay, az, ph);
+    }
+}
+
+// Near test of an (i-block, j-tile) pair of boxes: the gap between the
+// boxes is below gamma times the largest coordinate magnitude of either.
+__device__ __forceinline__ bool boxes_near(const float *bb, const float *tb, float gamma) {
+    float g2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gap = fmaxf(0.f, fmaxf(__ldg(tb + c) - bb[3 + c], bb[c] - __ldg(tb + 3 + c)));
+        g2 = fmaf(gap, gap, g2);
+    }
+    const float X = gamma * fmaxf(bb[6], __ldg(tb + 6));
+    return g2 < X * X;
+}
+
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT, bool NF>
 __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
     using namespace dev;
     constexpr int BI = NT * IR;
@@ -150,6 +214,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
 
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR];
     float mi[IR];
+    float bb[8];
     Acc<POL> acc[IR][4];
     const float2 eps2 = f2(p.eps2, p.eps2);
     int64_t b = 0, seg_begin = 0;
@@ -161,9 +226,14 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         if (q == 0 || jt == 0) {
             b = t / p.ntiles;
             seg_begin = jt;
+            if (NF) {
+                const int64_t u = b * (NT / 32) + (tid >> 5);  // this warp's box
+#pragma unroll
+                for (int e = 0; e < 8; ++e) bb[e] = __ldg(p.block_box + u * 8 + e);
+            }
 #pragma unroll
             for (int k = 0; k < IR; ++k) {
-                const int64_t i = b * BI + k * NT + tid;
+                const int64_t i = slot_of<NT, IR, NF>(b, k, tid);
                 const float x = p.soa[i], y = p.soa[p.Np + i], z = p.soa[2 * p.Np + i];
                 mi[k] = p.soa[3 * p.Np + i];
                 nx[k] = f2(-x, -x);
@@ -185,34 +255,24 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         const int s = (int)(q % ST);
         const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((q / ST) & 1), p.timeout);
         const float *sx = stages + s * NC * TJ;
-        const float *sy = sx + TJ;
-        const float *sz = sx + 2 * TJ;
-        const float *sm = sx + 3 * TJ;
-        const float *sxl = sx + (SPLIT ? 4 : 0) * TJ;
-        const float *syl = sx + (SPLIT ? 5 : 0) * TJ;
-        const float *szl = sx + (SPLIT ? 6 : 0) * TJ;
-
         float2 ax[IR], ay[IR], az[IR], ph[IR];
 #pragma unroll
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
-#pragma unroll 2
-        for (int jj = 0; jj < TJ; jj += 4) {
-            const float4 X = *reinterpret_cast<const float4 *>(sx + jj);
-            const float4 Y = *reinterpret_cast<const float4 *>(sy + jj);
-            const float4 Z = *reinterpret_cast<const float4 *>(sz + jj);
-            const float4 M = *reinterpret_cast<const float4 *>(sm + jj);
-            float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
-            if (SPLIT) {
-                XL = *reinterpret_cast<const float4 *>(sxl + jj);
-                YL = *reinterpret_cast<const float4 *>(syl + jj);
-                ZL = *reinterpret_cast<const float4 *>(szl + jj);
+        if (NF) {
+            // per (warp, 64-particle sub-tile): warp-uniform choice
+#pragma unroll 1
+            for (int c = 0; c < TJ / 64; ++c) {
+                const float *tb = p.tile_box + (jt * (TJ / 64) + c) * 8;
+                if (boxes_near(bb, tb, p.gamma))
+                    tile_pairs<IR, TJ, GUARD, true>(sx, 64 * c, 64 * c + 64, eps2, nx, ny, nz,
+                                                    nxl, nyl, nzl, ax, ay, az, ph);
+                else
+                    tile_pairs<IR, TJ, GUARD, false>(sx, 64 * c, 64 * c + 64, eps2, nx, ny, nz,
+                                                     nxl, nyl, nzl, ax, ay, az, ph);
             }
-            pair2<IR, GUARD, SPLIT>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(XL.x, XL.y),
-                                    f2(YL.x, YL.y), f2(ZL.x, ZL.y), f2(M.x, M.y), eps2, nx, ny,
-                                    nz, nxl, nyl, nzl, ax, ay, az, ph);
-            pair2<IR, GUARD, SPLIT>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(XL.z, XL.w),
-                                    f2(YL.z, YL.w), f2(ZL.z, ZL.w), f2(M.z, M.w), eps2, nx, ny,
-                                    nz, nxl, nyl, nzl, ax, ay, az, ph);
+        } else {
+            tile_pairs<IR, TJ, GUARD, SPLIT>(sx, 0, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, ax, ay,
+                                             az, ph);
         }
 #pragma unroll
         for (int k = 0; k < IR; ++k) {
@@ -241,7 +301,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         if (jt == p.ntiles - 1 || q == nq - 1) {
             // end of this CTA's segment of i-block b: tiles [seg_begin, jt]
             if (seg_begin == 0 && jt == p.ntiles - 1) {
-                force_epilogue<NT, IR, POL, GUARD>(p, b, acc, mi);
+                force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc, mi);
             } else {
                 const int slot = (b == first_block) ? 0 : 1;
                 Record *rec = p.records + (2 * c + slot) * BI;
@@ -268,7 +328,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
 #pragma unroll
                         for (int k = 0; k < IR; ++k) merge_record<POL>(acc[k], r + k * NT + tid);
                     }
-                    force_epilogue<NT, IR, POL, GUARD>(p, b, acc, mi);
+                    force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc, mi);
                     if (tid == 0) p.counters[b] = 0u;
                 }
             }
@@ -349,9 +409,9 @@ bool force_shape_compiled(const Shape &s) {
     return false;
 }
 
-template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT>
+template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT, bool NF>
 static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
-    auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT>;
+    auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT, NF>;
     const size_t smem = (size_t)ST * (SPLIT ? 7 : 4) * 4 * TJ + (size_t)ST * 8;
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
@@ -360,22 +420,25 @@ static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
     return NB_OK;
 }
 
+// mode: 0 single positions, 1 split, 2 adaptive (split near, single far;
+// never with the eps = 0 guard)
 template <int NT, int IR, int TJ, int ST, int POL>
-static int launch_sk_gs(const ForceParams &p, bool guard, bool split, int cps, cudaStream_t st) {
+static int launch_sk_gs(const ForceParams &p, bool guard, int mode, int cps, cudaStream_t st) {
     if (guard)
-        return split ? launch_sk<NT, IR, TJ, ST, POL, true, true>(p, cps, st)
-                     : launch_sk<NT, IR, TJ, ST, POL, true, false>(p, cps, st);
-    return split ? launch_sk<NT, IR, TJ, ST, POL, false, true>(p, cps, st)
-                 : launch_sk<NT, IR, TJ, ST, POL, false, false>(p, cps, st);
+        return mode ? launch_sk<NT, IR, TJ, ST, POL, true, true, false>(p, cps, st)
+                    : launch_sk<NT, IR, TJ, ST, POL, true, false, false>(p, cps, st);
+    if (mode == 2) return launch_sk<NT, IR, TJ, ST, POL, false, true, true>(p, cps, st);
+    return mode ? launch_sk<NT, IR, TJ, ST, POL, false, true, false>(p, cps, st)
+                : launch_sk<NT, IR, TJ, ST, POL, false, false, false>(p, cps, st);
 }
 
 template <int NT, int IR, int TJ, int ST>
-static int launch_sk_pol(const ForceParams &p, int pol, bool guard, bool split, int cps,
+static int launch_sk_pol(const ForceParams &p, int pol, bool guard, int mode, int cps,
                          cudaStream_t st) {
     switch (pol) {
-        case NB_PREC_FP32: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_FP32>(p, guard, split, cps, st);
-        case NB_PREC_KAHAN: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_KAHAN>(p, guard, split, cps, st);
-        case NB_PREC_F64ACC: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_F64ACC>(p, guard, split, cps, st);
+        case NB_PREC_FP32: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_FP32>(p, guard, mode, cps, st);
+        case NB_PREC_KAHAN: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_KAHAN>(p, guard, mode, cps, st);
+        case NB_PREC_F64ACC: return launch_sk_gs<NT, IR, TJ, ST, NB_PREC_F64ACC>(p, guard, mode, cps, st);
     }
     return fail(NB_ERR_UNSUPPORTED, "precision %d has no FP32-pair kernel", pol);
 }
@@ -411,7 +474,15 @@ int launch_force(const ForceJob &j) {
         return NB_OK;
     }
     float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
-    if (!j.packed_ready) {
+    const Shape &sh0 = j.shape;
+    const bool adaptive = j.adaptive && !guard;
+    char *sb = j.ws + j.L.sortbuf;
+    if (adaptive) {
+        int rc = launch_sorted_pack(j.pos, j.mass, j.N, j.L.Np, soa, sort_perm(sb, j.L),
+                                    sort_keys(sb), sort_box6(sb, j.L), sort_tile_boxes(sb, j.L),
+                                    64, sort_block_boxes(sb, j.L), 32 * sh0.ipt, j.stream);
+        if (rc) return rc;
+    } else if (!j.packed_ready) {
         int rc = launch_pack(j.pos, j.mass, j.N, j.L.Np, soa, j.stream);
         if (rc) return rc;
     }
@@ -434,9 +505,14 @@ int launch_force(const ForceJob &j) {
     p.counters = reinterpret_cast<uint32_t *>(j.ws + j.L.counters);
     p.status = status;
     p.timeout = j.timeout;
+    p.tile_box = adaptive ? sort_tile_boxes(sb, j.L) : nullptr;   // per 64 j-slots
+    p.block_box = adaptive ? sort_block_boxes(sb, j.L) : nullptr; // per warp (32 IR i-slots)
+    p.perm = adaptive ? sort_perm(sb, j.L) : nullptr;
+    p.gamma = j.gamma;
+    const int mode = adaptive ? 2 : (j.split ? 1 : 0);
 #define NB_DISPATCH(NT, IR, TJ, ST)                                                   \
     if (sh.threads == NT && sh.ipt == IR && sh.tile_j == TJ && sh.stages == ST)      \
-        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, j.split, sh.ctas_per_sm, \
+        return launch_sk_pol<NT, IR, TJ, ST>(p, j.precision, guard, mode, sh.ctas_per_sm, \
                                              j.stream);
     NB_FORCE_SHAPES(NB_DISPATCH)
 #undef NB_DISPATCH

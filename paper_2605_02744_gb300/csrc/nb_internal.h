@@ -59,6 +59,7 @@ struct WsLayout {
     size_t packA;     // float SoA [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
     size_t packB;     // float SoA [4][Np]: VJP cotangents (cx, cy, cz, pbar/3)
     size_t cot64;     // double SoA [4][Np]: the same cotangents in FP64
+    size_t sortbuf;   // Morton keys, permutation, tile/block boxes (adaptive path)
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
     size_t total;
@@ -95,6 +96,8 @@ struct ForceJob {
     double kick;
     int precision;
     bool split;         // hi/lo displacement (nb_positions resolved)
+    bool adaptive;      // Morton-sorted pack, hi/lo only for near tile pairs
+    float gamma;        // near/far threshold of the adaptive path
     bool packed_ready;  // packA already holds float positions of `pos`
     long long timeout;
     cudaStream_t stream;
@@ -105,6 +108,42 @@ struct ForceJob {
 
 // Resolves nb_opts::positions for a precision: true = split hi/lo.
 bool positions_split(const nb_opts *opts);
+// true when the split displacement is applied only to near tile pairs of a
+// Morton-sorted pack (explicit NB_POS_ADAPTIVE, or the default from N >= 2^16
+// for the KAHAN and F64ACC policies; 1/64 is the default near_gamma).
+bool positions_adaptive(const nb_opts *opts, int64_t N);
+
+// Well-separated threshold of the adaptive path: a (warp, 64-particle
+// sub-tile) pair takes the single-float displacement when the gap between
+// their boxes is at least gamma times the largest coordinate magnitude in
+// either box (per-pair relative displacement error <= ~sqrt(3) u / gamma,
+// u = 2^-24).  On the 2^20 Plummer and 65536 / 262144 log-normal workloads
+// the maximum relative acceleration error stayed at 1.2-2.9e-6 for every
+// gamma from 1/16 to 1/256; 1/64 keeps a factor-4 margin on the smallest.
+constexpr float kNearFarGamma = 0.015625f;
+
+// Sub-buffers of WsLayout::sortbuf.
+int64_t sort_keys_len(int64_t N);
+inline unsigned long long *sort_keys(char *sb) { return reinterpret_cast<unsigned long long *>(sb); }
+inline int *sort_perm(char *sb, const WsLayout &L) {
+    return reinterpret_cast<int *>(sb + 8 * sort_keys_len(L.Np));
+}
+inline float *sort_tile_boxes(char *sb, const WsLayout &L) {
+    return reinterpret_cast<float *>(sb + 8 * sort_keys_len(L.Np) + 4 * L.Np);
+}
+inline float *sort_block_boxes(char *sb, const WsLayout &L) {
+    return sort_tile_boxes(sb, L) + 8 * (L.Np / 64 + 1);
+}
+inline long long *sort_box6(char *sb, const WsLayout &L) {
+    return reinterpret_cast<long long *>(sort_block_boxes(sb, L) + 8 * (L.Np / 32 + 1));
+}
+inline size_t sortbuf_bytes(int64_t Np) {
+    return 8 * (size_t)sort_keys_len(Np) + 4 * (size_t)Np + 32 * (size_t)(Np / 64 + 1) +
+           32 * (size_t)(Np / 32 + 1) + 64;
+}
+int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
+                       int *perm, unsigned long long *keys, long long *box6, float *tile_boxes,
+                       int tile_unit, float *block_boxes, int block_unit, cudaStream_t st);
 
 // Number of float arrays of Np entries in a packed position buffer.
 constexpr int kPackArrays = 7;

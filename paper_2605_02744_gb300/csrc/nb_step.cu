@@ -21,7 +21,8 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ pos, double *__restr
                                        const double *__restrict__ mass, int64_t N, int64_t Np,
                                        double dt, float *__restrict__ soa) {
     const double half = 0.5 * dt;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Np;
+    const int64_t n_iter = soa ? Np : N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_iter;
          i += (int64_t)gridDim.x * blockDim.x) {
         float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
         float m = 0.f;
@@ -37,7 +38,7 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ pos, double *__restr
             }
             m = __double2float_rn(mass[i]);
         }
-        store_packed(soa, Np, i, hi, lo, m);
+        if (soa) store_packed(soa, Np, i, hi, lo, m);
     }
 }
 

@@ -130,3 +130,44 @@ def test_plummer_2pow20_sampled_rows(prec):
     ea = rel_vec_err(host(a)[rows], ra)
     ep = rel_err(host(p)[rows], rp)
     assert ea.max() <= 1e-5 and ep.max() <= 1e-5, (ea.max(), ep.max())
+
+
+@pytest.mark.parametrize("n,eps", [(8191, 0.01), (20001, 1e-3), (70001, 1e-3), (300001, 1e-3)])
+@pytest.mark.parametrize("prec", ["kahan", "f64acc"])
+def test_adaptive_positions(n, eps, prec):
+    # Morton-sorted pack, hi/lo displacement only for near tile pairs
+    s = ics.plummer_lognormal(n, seed=n)
+    o = binding.make_opts(prec, positions="adaptive")
+    acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = binding.workspace(n, 1, o)
+    binding.nb_forces(dev(s.pos), dev(s.mass), eps, acc, pot, ws, o)
+    assert binding.nb_poll_status(ws, o) == binding.NB_OK
+    if n <= 20001:
+        ra, rp = oracle.forces(s.pos, s.mass, eps)
+        a, p = host(acc), host(pot)
+    else:
+        rows = np.concatenate([np.random.default_rng(1).choice(n, 1500, replace=False),
+                               np.argsort(np.linalg.norm(s.pos, axis=1))[:64]])
+        ra, rp = oracle.forces_rows(s.pos, s.mass, eps, rows)
+        a, p = host(acc)[rows], host(pot)[rows]
+    assert rel_vec_err(a, ra).max() <= 1e-5 and rel_err(p, rp).max() <= 1e-5
+    # deterministic: sorting keys are unique
+    acc2 = torch.empty_like(acc)
+    binding.nb_forces(dev(s.pos), dev(s.mass), eps, acc2, None, ws, o)
+    assert torch.equal(acc, acc2)
+
+
+def test_adaptive_step_matches_split_step():
+    s = ics.plummer(70000, seed=3)
+    a = api.System(s.pos, s.vel, s.mass, 1e-3, precision="f64acc")
+    a.opts.positions = binding.NB_POS_ADAPTIVE
+    b = api.System(s.pos, s.vel, s.mass, 1e-3, precision="f64acc")
+    b.opts.positions = binding.NB_POS_SPLIT
+    a.step(1e-4, 3)
+    b.step(1e-4, 3)
+    assert a.poll() == binding.NB_OK
+    ea = rel_vec_err(host(a.acc), host(b.acc)).max()
+    assert ea <= 2e-5, ea
+    dx = np.abs(host(a.pos) - host(b.pos)).max()
+    assert dx <= 1e-12, dx
