@@ -238,7 +238,10 @@ int nb_energy(const nb_state *s, double *out3, const nb_opts *opts);
  * with d = x_j - x_k, s^2 = |d|^2 + eps^2, K(d) = s^-3 I - 3 s^-5 d d^T.
  * acc_bar [N][3] in; pot_bar [N] in or NULL (zero); pos_bar [N][3] and
  * mass_bar [N] out, overwritten.  Derived from Eq. 1; the paper itself does
- * not differentiate its simulation.
+ * not differentiate its simulation.  The VJP kernels form displacements
+ * from single FP32 positions unless opts->positions is NB_POS_SPLIT
+ * (gradients tolerate the ~1e-5 displacement error; the adjoint tests gate
+ * FP32-pair gradients at 1e-4 median / 1e-3 max against FP64).
  */
 int nb_forces_vjp(const double *pos, const double *mass, int64_t N, double eps,
                   const double *acc_bar, const double *pot_bar, double *pos_bar,

@@ -189,6 +189,7 @@ struct VjpJob {
     double rewind_kick;
     double rewind_drift;
     int precision;
+    bool split;  // hi/lo displacement (the VJP's default is single floats)
     long long timeout;
     cudaStream_t stream;
     char *ws;

@@ -98,7 +98,7 @@ __global__ void pack_cotangent_kernel(const double *__restrict__ abar,
 // is skipped by index, so the large self terms never enter a sum.  The
 // per-k constants arrive negated (nmk = -m_k, npbk = -pbar_k/3), which makes
 // the running sums C and q carry the opposite sign (x_bar uses +3C).
-template <int IR, bool GUARD, bool PB, bool FUSED>
+template <int IR, bool GUARD, bool PB, bool FUSED, bool SPLIT>
 __device__ __forceinline__ void vjp_pair2(
     const int jj, const int (&kr)[IR], const float2 xj, const float2 yj, const float2 zj,
     const float2 xl, const float2 yl, const float2 zl, const float2 mj, const float2 cxj,
@@ -110,9 +110,14 @@ __device__ __forceinline__ void vjp_pair2(
     using namespace dev;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
-        const float2 dx = add2(add2(xj, nx[k]), add2(xl, nxl[k]));
-        const float2 dy = add2(add2(yj, ny[k]), add2(yl, nyl[k]));
-        const float2 dz = add2(add2(zj, nz[k]), add2(zl, nzl[k]));
+        float2 dx = add2(xj, nx[k]);
+        float2 dy = add2(yj, ny[k]);
+        float2 dz = add2(zj, nz[k]);
+        if (SPLIT) {
+            dx = add2(dx, add2(xl, nxl[k]));
+            dy = add2(dy, add2(yl, nyl[k]));
+            dz = add2(dz, add2(zl, nzl[k]));
+        }
         float2 r2 = fma2(dx, dx, eps2);
         r2 = fma2(dy, dy, r2);
         r2 = fma2(dz, dz, r2);
@@ -211,7 +216,7 @@ __device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b,
     if (bad) dev::set_status(p.status, kStatusNonFinite);
 }
 
-template <int NT, int IR, int TJ, int ST, bool GUARD, bool PB, bool FUSED>
+template <int NT, int IR, int TJ, int ST, bool GUARD, bool PB, bool FUSED, bool SPLIT>
 __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
     using namespace dev;
     constexpr int BI = NT * IR;
@@ -306,12 +311,12 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
 #pragma unroll
             for (int comp = 0; comp < NC; ++comp)
                 V[comp] = *reinterpret_cast<const float4 *>(st + comp * TJ + jj);
-            vjp_pair2<IR, GUARD, PB, FUSED>(
+            vjp_pair2<IR, GUARD, PB, FUSED, SPLIT>(
                 jj, kr, f2(V[0].x, V[0].y), f2(V[1].x, V[1].y), f2(V[2].x, V[2].y), f2(V[4].x, V[4].y),
                 f2(V[5].x, V[5].y), f2(V[6].x, V[6].y), f2(V[3].x, V[3].y), f2(V[7].x, V[7].y),
                 f2(V[8].x, V[8].y), f2(V[9].x, V[9].y), f2(V[10].x, V[10].y), eps2, nx, ny, nz,
                 nxl, nyl, nzl, nmk, cxk, cyk, czk, npbk, S);
-            vjp_pair2<IR, GUARD, PB, FUSED>(
+            vjp_pair2<IR, GUARD, PB, FUSED, SPLIT>(
                 jj + 2, kr, f2(V[0].z, V[0].w), f2(V[1].z, V[1].w), f2(V[2].z, V[2].w), f2(V[4].z, V[4].w),
                 f2(V[5].z, V[5].w), f2(V[6].z, V[6].w), f2(V[3].z, V[3].w), f2(V[7].z, V[7].w),
                 f2(V[8].z, V[8].w), f2(V[9].z, V[9].w), f2(V[10].z, V[10].w), eps2, nx, ny, nz,
@@ -466,6 +471,8 @@ __global__ void __launch_bounds__(NT)
 // ---------------------------------------------------------- dispatch
 #define NB_VJP_SHAPES(X) \
     X(128, 2, 128, 3)    \
+    X(256, 2, 128, 3)    \
+    X(256, 1, 128, 3)    \
     X(128, 1, 64, 2)
 
 bool vjp_shape_compiled(const Shape &s) {
@@ -476,9 +483,9 @@ bool vjp_shape_compiled(const Shape &s) {
     return false;
 }
 
-template <int NT, int IR, int TJ, int ST, bool GUARD, bool PB, bool FUSED>
+template <int NT, int IR, int TJ, int ST, bool GUARD, bool PB, bool FUSED, bool SPLIT>
 static int launch_vjp_sk(const VjpParams &p, int cps, cudaStream_t st) {
-    auto kern = vjp_sk_kernel<NT, IR, TJ, ST, GUARD, PB, FUSED>;
+    auto kern = vjp_sk_kernel<NT, IR, TJ, ST, GUARD, PB, FUSED, SPLIT>;
     const size_t smem = (size_t)ST * 11 * 4 * TJ + (size_t)ST * 8;
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
@@ -487,20 +494,26 @@ static int launch_vjp_sk(const VjpParams &p, int cps, cudaStream_t st) {
     return NB_OK;
 }
 
-template <int NT, int IR, int TJ, int ST>
-static int launch_vjp_variant(const VjpParams &p, bool guard, bool pb, bool fused, int cps,
-                              cudaStream_t st) {
+template <int NT, int IR, int TJ, int ST, bool SPLIT>
+static int launch_vjp_variant2(const VjpParams &p, bool guard, bool pb, bool fused, int cps,
+                               cudaStream_t st) {
     if (fused && pb) return fail(NB_ERR_UNSUPPORTED, "fused force with pot_bar is not built");
     if (guard) {
-        if (fused) return launch_vjp_sk<NT, IR, TJ, ST, true, false, true>(p, cps, st);
-        return pb ? launch_vjp_sk<NT, IR, TJ, ST, true, true, false>(p, cps, st)
-                  : launch_vjp_sk<NT, IR, TJ, ST, true, false, false>(p, cps, st);
+        if (fused) return launch_vjp_sk<NT, IR, TJ, ST, true, false, true, SPLIT>(p, cps, st);
+        return pb ? launch_vjp_sk<NT, IR, TJ, ST, true, true, false, SPLIT>(p, cps, st)
+                  : launch_vjp_sk<NT, IR, TJ, ST, true, false, false, SPLIT>(p, cps, st);
     }
-    if (fused) return launch_vjp_sk<NT, IR, TJ, ST, false, false, true>(p, cps, st);
-    return pb ? launch_vjp_sk<NT, IR, TJ, ST, false, true, false>(p, cps, st)
-              : launch_vjp_sk<NT, IR, TJ, ST, false, false, false>(p, cps, st);
+    if (fused) return launch_vjp_sk<NT, IR, TJ, ST, false, false, true, SPLIT>(p, cps, st);
+    return pb ? launch_vjp_sk<NT, IR, TJ, ST, false, true, false, SPLIT>(p, cps, st)
+              : launch_vjp_sk<NT, IR, TJ, ST, false, false, false, SPLIT>(p, cps, st);
 }
 
+template <int NT, int IR, int TJ, int ST>
+static int launch_vjp_variant(const VjpParams &p, bool guard, bool pb, bool fused, bool split,
+                              int cps, cudaStream_t st) {
+    return split ? launch_vjp_variant2<NT, IR, TJ, ST, true>(p, guard, pb, fused, cps, st)
+                 : launch_vjp_variant2<NT, IR, TJ, ST, false>(p, guard, pb, fused, cps, st);
+}
 
 int launch_vjp(const VjpJob &j) {
     const bool guard = (j.eps == 0.0);
@@ -560,7 +573,8 @@ int launch_vjp(const VjpJob &j) {
     p.timeout = j.timeout;
 #define NB_DISPATCH(NT, IR, TJ, ST)                                              \
     if (sh.threads == NT && sh.ipt == IR && sh.tile_j == TJ && sh.stages == ST) \
-        return launch_vjp_variant<NT, IR, TJ, ST>(p, guard, pb, fused, sh.ctas_per_sm, j.stream);
+        return launch_vjp_variant<NT, IR, TJ, ST>(p, guard, pb, fused, j.split, sh.ctas_per_sm, \
+                                                  j.stream);
     NB_VJP_SHAPES(NB_DISPATCH)
 #undef NB_DISPATCH
     return fail(NB_ERR_UNSUPPORTED, "VJP kernel shape (%d,%d,%d,%d) not compiled", sh.threads,

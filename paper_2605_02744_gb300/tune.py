@@ -28,6 +28,10 @@ FORCE_CANDIDATES = [
     for c in (1, 2, 4)
 ]
 BATCHED_CANDIDATES = [dict(cluster_ctas=c) for c in (2, 4, 8)]
+VJP_CANDIDATES = [
+    dict(threads=t, i_per_thread=i, tile_j=j, stages=s, ctas_per_sm=4)
+    for (t, i, j, s) in [(128, 2, 128, 3), (256, 2, 128, 3), (256, 1, 128, 3), (128, 1, 64, 2)]
+]
 
 
 def cache_path() -> str:
