@@ -313,15 +313,17 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        n0 = binding.nb_launch_count()
         with ClockSampler(dev.index or 0) as clk:
             times = _time_steps(system, DT_MAIN, args.steps, flush, torch)
         torch.cuda.synchronize()
+        launches = binding.nb_launch_count() - n0
         assert system.poll() == binding.NB_OK
-        results[prec] = (times, clk.summary())
+        results[prec] = (times, clk.summary(), launches)
         del system
         torch.cuda.empty_cache()
 
-    times, clocks = results["kahan"]
+    times, clocks, kahan_launches = results["kahan"]
     total_ms = sum(times)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -397,27 +399,27 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "Plummer sphere N=2^20 (1048576), equal mass, seed 0, eps=1e-3; "
-                               "one KDK step dt=1e-4 (FP32 pairs, Kahan accumulation, FP64 "
-                               "state) + energy",
+                               "one KDK step dt=1e-4 (FP32 pairs, Kahan accumulation, "
+                               "adaptive hi/lo displacement, FP64 state) + energy",
                    "N": N_MAIN, "precision": "kahan", "interactions_per_step": "N^2",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "force_sk_kernel<256,4,256,3,KAHAN>",
+                     "kernel": "force_sk_kernel<256,4,256,3,KAHAN,split,adaptive>",
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{max_mhz:.0f} MHz (max SM clock)",
                      "frac_at_observed_clock": (achieved / (peak_tflops * obs / max_mhz)
                                                 if obs else None),
                      "timing": "CUDA events around each nb_step+nb_energy (force kernel "
-                               "plus O(N) kernels) on the launching stream"},
+                               "plus the O(N) and sort kernels) on the launching stream"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "how": "pinned host pos/vel/mass -> device, nb_step (priming force + 1 KDK "
                        "step), nb_energy, pos/vel/acc/pot/energy -> host; wall clock"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": kahan_launches,
         "variants": {"f64acc_value": ws * args.steps * inter / (sum(results["f64acc"][0]) * 1e-3)
                      / 1e9, "f64acc_ms_per_step": f64_ms,
                      "kahan_ms_per_step": step_ms,

@@ -120,6 +120,10 @@ const char *nb_version(void);
 /* Message for the last failing call on this host thread ("" if none). */
 const char *nb_last_error(void);
 
+/* Number of kernels this library has enqueued in this process (all host
+ * threads).  Kernels replayed from a captured CUDA graph are not counted. */
+unsigned long long nb_launch_count(void);
+
 /* 1 if `tune` names a kernel shape compiled into this build, else 0. */
 int nb_tune_valid(const nb_tune *tune);
 

@@ -39,7 +39,7 @@ POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
-            "nb_forces_noalloc")
+            "nb_forces_noalloc", "nb_launch_count")
 
 
 class NbError(RuntimeError):
@@ -85,6 +85,7 @@ _SIGS = {
     "nb_opts_default": (None, [_OPTS]),
     "nb_version": (ctypes.c_char_p, []),
     "nb_last_error": (ctypes.c_char_p, []),
+    "nb_launch_count": (ctypes.c_ulonglong, []),
     "nb_tune_valid": (ctypes.c_int, [ctypes.POINTER(nb_tune)]),
     "nb_workspace_bytes": (_sz, [_i64, _i32, _OPTS]),
     "nb_forces": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _sz, _OPTS]),
@@ -169,6 +170,10 @@ def nb_version() -> str:
 
 def nb_last_error() -> str:
     return lib().nb_last_error().decode()
+
+
+def nb_launch_count() -> int:
+    return int(lib().nb_launch_count())
 
 
 def nb_tune_valid(tune) -> bool:

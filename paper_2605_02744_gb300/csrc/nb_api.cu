@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -30,6 +31,9 @@ void clear_error() { g_err[0] = '\0'; }
 int cuda_check(cudaError_t e, const char *what) {
     return fail(NB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------- device
 int device_sm_count() {
@@ -253,6 +257,8 @@ const char *nb_version(void) {
 }
 
 const char *nb_last_error(void) { return g_err; }
+
+unsigned long long nb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int nb_tune_valid(const nb_tune *t) {
     if (!t) return 0;

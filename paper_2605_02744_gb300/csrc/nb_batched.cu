@@ -339,6 +339,7 @@ static int launch_batched_cs(const BatchedParams &p, cudaStream_t st) {
     if (nclusters > kBMaxSlots) nclusters = kBMaxSlots;
     cfg.gridDim = dim3(CS * nclusters, 1, 1);
     NB_CUDA(cudaLaunchKernelEx(&cfg, kern, p));
+    count_launch();
     return NB_OK;
 }
 
@@ -390,6 +391,7 @@ int launch_batched(const BatchedJob &j) {
         batched_setup_kernel<<<1, 1024, smem, j.stream>>>(j.offsets, j.B, j.N, j.eps,
                                                           const_cast<int *>(p.order), p.counter,
                                                           p.status);
+        count_launch();
         NB_CUDA(cudaGetLastError());
     }
     const int cs = j.cluster > 0 ? j.cluster : 8;

@@ -57,6 +57,7 @@ int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, fl
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>(cdiv(Np, threads), 8192);
     pack_soa_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, mass, N, Np, soa);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -416,6 +417,7 @@ static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -464,6 +466,7 @@ int launch_force(const ForceJob &j) {
     if (j.precision == NB_PREC_FP64) {
         constexpr int NT = 128;
         const int64_t grid = cdiv(j.N, NT);
+        count_launch();
         if (guard)
             force_fp64_kernel<NT, true><<<(unsigned)grid, NT, 0, j.stream>>>(
                 j.pos, j.mass, j.N, 0.0, j.G, j.acc, j.pot, j.vel, j.kick, status);

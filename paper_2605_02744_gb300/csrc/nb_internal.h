@@ -46,6 +46,9 @@ bool shape_compiled(const Shape &s, int kind);
 enum Kind { kKindForce = 0, kKindVjp = 1 };
 
 int device_sm_count();
+// Counts kernels this library enqueued (nb_launch_count); a CUDA-graph
+// replay launches the captured kernels without passing through here.
+void count_launch(int n = 1);
 // Resident CTAs per SM of `kernel` (>= 1), and the persistent grid size:
 // min(requested CTAs per SM, occupancy) x SMs, capped at `total` items.
 int occupancy(const void *kernel, int threads, size_t smem);

@@ -233,26 +233,35 @@ int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t
     const int64_t P = sort_keys_len(N);
     const int threads = 256;
     bbox_init_kernel<<<1, 32, 0, st>>>(box6);
+    count_launch();
     const int64_t gb = std::min<int64_t>(cdiv(N, threads), 1024);
     bbox_kernel<<<(unsigned)gb, threads, 0, st>>>(pos, N, box6);
+    count_launch();
     morton_keys_kernel<<<(unsigned)std::min<int64_t>(cdiv(P, threads), 8192), threads, 0, st>>>(
         pos, N, P, box6, keys);
+    count_launch();
     const unsigned nchunks = (unsigned)(P / kSortChunk);
     bitonic_smem_kernel<<<nchunks, 1024, 0, st>>>(keys, 2, kSortChunk);
+    count_launch();
     for (int64_t k = 2 * kSortChunk; k <= P; k <<= 1) {
         for (int64_t j = k >> 1; j >= kSortChunk; j >>= 1) {
             bitonic_global_kernel<<<(unsigned)std::min<int64_t>(cdiv(P / 2, threads), 8192),
                                     threads, 0, st>>>(keys, P, k, j);
+            count_launch();
         }
         bitonic_smem_kernel<<<nchunks, 1024, 0, st>>>(keys, k, k);
+        count_launch();
     }
     pack_sorted_kernel<<<(unsigned)std::min<int64_t>(cdiv(Np, threads), 8192), threads, 0, st>>>(
         pos, mass, keys, N, Np, soa, perm);
+    count_launch();
     // every unit up to Np: units past N get an empty box (never near)
     slot_boxes_kernel<<<(unsigned)(Np / tile_unit), 256, 0, st>>>(soa, N, Np, tile_unit,
                                                                   tile_boxes);
+    count_launch();
     slot_boxes_kernel<<<(unsigned)(Np / block_unit), 256, 0, st>>>(soa, N, Np, block_unit,
                                                                    block_boxes);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -48,6 +48,7 @@ int launch_kick_drift_pack(double *pos, double *vel, const double *acc, const do
     const int64_t blocks = std::min<int64_t>(cdiv(Np, threads), 8192);
     kick_drift_pack_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, vel, acc, mass, N, Np, dt,
                                                                  soa);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -103,9 +104,11 @@ int launch_energy(const double *vel, const double *mass, const double *pot, int6
     const int blocks = (int)std::min<int64_t>(cdiv(N, kEnergyThreads), kEnergyMaxBlocks);
     double *partial = reinterpret_cast<double *>(ws + L.scratch);
     energy_partial_kernel<<<blocks, kEnergyThreads, 0, st>>>(vel, mass, pot, N, partial);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     energy_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out3,
                                           reinterpret_cast<uint32_t *>(ws + L.status));
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -490,6 +490,7 @@ static int launch_vjp_sk(const VjpParams &p, int cps, cudaStream_t st) {
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -528,6 +529,7 @@ int launch_vjp(const VjpJob &j) {
         pack_cotangent_kernel<<<(unsigned)blocks, threads, 0, j.stream>>>(
             j.acc_bar, j.pot_bar, j.vel_bar, j.pos_bar, j.drift_dt, j.kick_coef,
             j.step_form ? 1 : 0, j.N, j.L.Np, csoa, cdbl);
+        count_launch();
         NB_CUDA(cudaGetLastError());
     }
     if (j.precision == NB_PREC_FP64) {
@@ -539,6 +541,7 @@ int launch_vjp(const VjpJob &j) {
                                                j.G, j.pos_bar, j.mass_bar, j.accumulate ? 1 : 0,
                                                j.acc_out, j.vhalf, j.pos_rw, j.rewind_kick,
                                                j.rewind_drift, status);
+        count_launch();
         NB_CUDA(cudaGetLastError());
         return NB_OK;
     }
