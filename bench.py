@@ -251,6 +251,42 @@ def batched_rate(torch, steps=1000):
             "interactions": inter}
 
 
+def paper_workload(torch):
+    """The paper's benchmark size (Sec. 4.2): 409600 particles, 3 steps of a
+    Hermite scheme with acceleration + jerk (here fourth order; the paper's is
+    sixth order and runs its predictor/corrector on the host).  Context for
+    its Table 1, not a like-for-like comparison."""
+    from paper_2605_02744_gb300 import binding, ics
+    n, steps, eps, dt = 409600, 3, 1e-3, 1e-3
+    s = ics.plummer(n, seed=0)
+    o = binding.make_opts("kahan")
+    pos = torch.tensor(s.pos, device="cuda")
+    vel = torch.tensor(s.vel, device="cuda")
+    mass = torch.tensor(s.mass, device="cuda")
+    acc = torch.empty_like(pos)
+    jerk = torch.empty_like(pos)
+    ws = binding.workspace(n, 1, o)
+    binding.nb_hermite4(pos, vel, mass, eps, acc, jerk, False, dt, 1, ws, o)  # warm-up
+    pos.copy_(torch.tensor(s.pos, device="cuda"))
+    vel.copy_(torch.tensor(s.vel, device="cuda"))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    binding.nb_hermite4(pos, vel, mass, eps, acc, jerk, False, dt, steps, ws, o)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    evals = steps + 1
+    return {"workload": "Plummer N=409600, eps=1e-3, 3 Hermite-4 steps dt=1e-3 "
+                        "(acceleration + jerk, FP32 pairs, Kahan), including the first "
+                        "evaluation", "seconds": ms / 1e3,
+            "acc_jerk_interactions_per_s": evals * float(n) * n / (ms * 1e-3),
+            "paper_seconds": {"wormhole_n300_1chip": 1459.46,
+                              "cpu_2x_epyc9124_32threads": 2875.39},
+            "note": "paper: sixth-order Hermite, host FP64 predictor/corrector, whole run"}
+
+
 def variant_rates(torch):
     """One force+potential at the 65536-particle log-normal workload per variant."""
     from paper_2605_02744_gb300 import api, ics
@@ -365,7 +401,7 @@ def run_ours(args):
     d2h = sum(v.numel() * 8 for v in outs.values()) + 24
     del e2e_sys
 
-    adj = batched = variants = None
+    adj = batched = variants = paper = None
     if not args.skip_adjoint:
         try:
             adj = adjoint_ratio(torch)
@@ -380,6 +416,10 @@ def run_ours(args):
             variants = variant_rates(torch)
         except Exception as e:
             variants = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            paper = paper_workload(torch)
+        except Exception as e:
+            paper = {"error": f"{type(e).__name__}: {e}"}
 
     if rank != 0:
         if ws > 1:
@@ -426,6 +466,7 @@ def run_ours(args):
                      "lognormal_65536_per_precision": variants},
         "adjoint": adj,
         "batched": batched,
+        "paper_workload": paper,
     }
     if ws == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -289,6 +289,35 @@ int nb_step_vjp_reverse(double *pos, double *vhalf, double *acc, const double *m
                         void *ws, size_t ws_bytes, const nb_opts *opts);
 
 /*
+ * Acceleration, jerk and potential at (pos, vel): the quantities of the
+ * paper's pair kernel (App. A, Algorithm 3; jerk = time derivative of the
+ * acceleration along the motion),
+ *   jerk_i = G sum_{j != i} m_j [ (v_j - v_i) / s^3 - 3 ((x_j - x_i).(v_j - v_i)) (x_j - x_i) / s^5 ]
+ * with s^2 = |x_j - x_i|^2 + eps^2.  pos, vel, acc, jerk [N][3]; mass, pot
+ * [N] (pot nullable).  FP32 pairs from split hi/lo positions and FP32
+ * velocities; precision FP32, KAHAN or F64ACC (FP64 returns
+ * NB_ERR_UNSUPPORTED).
+ */
+int nb_forces_jerk(const double *pos, const double *vel, const double *mass, int64_t N,
+                   double eps, double *acc, double *jerk, double *pot, void *ws, size_t ws_bytes,
+                   const nb_opts *opts);
+
+/*
+ * nsteps of the fourth-order Hermite predictor-corrector around the
+ * acceleration + jerk evaluation (the predict / evaluate / correct cycle of
+ * Sec. 2.1, at fourth order; the paper's own integrator is sixth order):
+ *   xp = x + v h + a h^2/2 + j h^3/6,  vp = v + a h + j h^2/2
+ *   a1, j1 = evaluation at (xp, vp)
+ *   v <- v + (a + a1) h/2 + (j - j1) h^2/12,  x <- x + (v_old + v) h/2 + (a - a1) h^2/12
+ * acc/jerk must hold a(x), j(x) when acc_valid != 0 (else they are computed
+ * first) and hold the last evaluation on return.  Other arguments as
+ * nb_forces_jerk.
+ */
+int nb_hermite4(double *pos, double *vel, const double *mass, int64_t N, double eps, double *acc,
+                double *jerk, int32_t acc_valid, double dt, int64_t nsteps, void *ws,
+                size_t ws_bytes, const nb_opts *opts);
+
+/*
  * Synchronises `stream`, reads the device status word latched in ws (a
  * bitwise OR of 1 << NB_ERR_TIMEOUT and 1 << NB_ERR_NONFINITE), clears it,
  * and returns the matching NB_ERR_* code (timeout first) or NB_OK.

@@ -9,8 +9,10 @@ Contents
 --------
 * ``nbody_oracle.c`` -- plain double-precision C (OpenMP over the output index
   only): forces + potential (Eq. 1 of Sec. 2.1 with Plummer softening), exact
-  rows for a subset, kick-drift-kick leapfrog, energy, and the force
-  vector-Jacobian product written block by block from the chain rule.
+  rows for a subset, kick-drift-kick leapfrog, energy, the force
+  vector-Jacobian product written block by block from the chain rule, and
+  acceleration + jerk (App. A, Algorithm 3) with a fourth-order Hermite
+  predictor-corrector.
 * this module -- ctypes wrappers, the discrete adjoint of one KDK step taken
   term by term (two separate force VJPs per step, never merged), the adjoint
   of a whole trajectory, and the final-position loss.
@@ -80,6 +82,13 @@ def _load():
             lib.orc_energy.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp]
             lib.orc_forces_vjp.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
                                            ctypes.c_double, _dp, _dp, _dp, _dp]
+            lib.orc_forces_jerk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                            ctypes.c_double, _dp, _dp, _dp]
+            lib.orc_forces_jerk_rows.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int64, _i64p, _dp, _dp]
+            lib.orc_hermite4.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.c_int, _dp, _dp]
             _lib = lib
     return _lib
 
@@ -168,6 +177,47 @@ def forces_vjp(pos, mass, eps: float, abar, phibar=None, G: float = 1.0):
     _load().orc_forces_vjp(n, _ptr(pos), _ptr(mass), float(eps), float(G), _ptr(abar),
                            _ptr(phibar), _ptr(xbar), _ptr(mbar))
     return xbar, mbar
+
+
+def forces_jerk(pos, vel, mass, eps: float, G: float = 1.0):
+    """(acc, jerk, pot): the quantities of App. A, Algorithm 3 (+ potential)."""
+    mass = _f64(mass)
+    n = mass.shape[0]
+    pos = _f64(pos, (n, 3))
+    vel = _f64(vel, (n, 3))
+    acc = np.empty((n, 3))
+    jerk = np.empty((n, 3))
+    pot = np.empty(n)
+    _load().orc_forces_jerk(n, _ptr(pos), _ptr(vel), _ptr(mass), float(eps), float(G),
+                            _ptr(acc), _ptr(jerk), _ptr(pot))
+    return acc, jerk, pot
+
+
+def forces_jerk_rows(pos, vel, mass, eps: float, rows, G: float = 1.0):
+    """Exact (acc, jerk) for the particles listed in ``rows`` against all N."""
+    mass = _f64(mass)
+    n = mass.shape[0]
+    pos = _f64(pos, (n, 3))
+    vel = _f64(vel, (n, 3))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    acc = np.empty((rows.size, 3))
+    jerk = np.empty((rows.size, 3))
+    _load().orc_forces_jerk_rows(n, _ptr(pos), _ptr(vel), _ptr(mass), float(eps), float(G),
+                                 rows.size, rows.ctypes.data_as(_i64p), _ptr(acc), _ptr(jerk))
+    return acc, jerk
+
+
+def hermite4(pos, vel, mass, eps: float, h: float, nsteps: int, G: float = 1.0):
+    """nsteps of fourth-order Hermite; returns (pos, vel, acc, jerk)."""
+    mass = _f64(mass)
+    n = mass.shape[0]
+    pos = _f64(pos, (n, 3)).copy()
+    vel = _f64(vel, (n, 3)).copy()
+    acc = np.empty((n, 3))
+    jerk = np.empty((n, 3))
+    _load().orc_hermite4(n, _ptr(pos), _ptr(vel), _ptr(mass), float(eps), float(G), float(h),
+                         int(nsteps), 0, _ptr(acc), _ptr(jerk))
+    return pos, vel, acc, jerk
 
 
 def kdk_step_adjoint(x_n, x_np1, mass, eps: float, h: float, xbar, vbar, mbar, G: float = 1.0):

@@ -21,6 +21,10 @@
  *       x_{n+1}   = x_n + h v_{n+1/2}
  *       v_{n+1}   = v_{n+1/2} + (h/2) a(x_{n+1})
  *   energy:  K = 1/2 sum m_i |v_i|^2,  W = 1/2 sum m_i phi_i,  E = K + W
+ *   jerk (App. A, Algorithm 3): the time derivative of a_i along the motion,
+ *       j_i = G sum_{j != i} m_j [ (v_j - v_i) / s^3 - 3 (d . (v_j - v_i)) d / s^5 ]
+ *   fourth-order Hermite predictor-corrector (Sec. 2.1's predict, evaluate,
+ *   correct cycle, at fourth rather than sixth order)
  *   force vector-Jacobian product, from the chain rule written out block by
  *   block (J_ik = d a_i / d x_k, a 3x3 matrix):
  *       xbar_k = sum_i J_ik^T abar_i + sum_i (d phi_i / d x_k) phibar_i
@@ -36,6 +40,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -211,5 +216,112 @@ void orc_forces_vjp(int64_t N, const double *pos, const double *mass, double eps
         xbar[3 * k + 1] = xb[1];
         xbar[3 * k + 2] = xb[2];
         mbar[k] = mb;
+    }
+}
+
+/*
+ * Acceleration, jerk (its time derivative along the motion) and potential:
+ * the quantities of the pair kernel in App. A, Algorithm 3, with the same
+ * softening.  For d = x_j - x_i, w = v_j - v_i, s^2 = |d|^2 + eps^2:
+ *   jerk_i = G sum_{j != i} m_j [ w / s^3 - 3 (d . w) d / s^5 ]
+ */
+void orc_forces_jerk(int64_t N, const double *pos, const double *vel, const double *mass,
+                     double eps, double G, double *acc, double *jerk, double *pot) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+        double a[3] = {0, 0, 0}, jk[3] = {0, 0, 0}, phi = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double d[3], w[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = pos[3 * j + c] - pos[3 * i + c];
+                w[c] = vel[3 * j + c] - vel[3 * i + c];
+            }
+            const double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+            if (s2 == 0.0) continue;
+            const double s = sqrt(s2);
+            const double inv3 = 1.0 / (s2 * s);
+            const double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+            for (int c = 0; c < 3; ++c) {
+                a[c] += mass[j] * d[c] * inv3;
+                jk[c] += mass[j] * (w[c] * inv3 - 3.0 * dw * d[c] * inv3 / s2);
+            }
+            phi -= mass[j] / s;
+        }
+        for (int c = 0; c < 3; ++c) {
+            acc[3 * i + c] = G * a[c];
+            jerk[3 * i + c] = G * jk[c];
+        }
+        if (pot) pot[i] = G * phi;
+    }
+}
+
+/*
+ * nsteps of the fourth-order Hermite predictor-corrector (the
+ * predict-evaluate-correct cycle of Sec. 2.1 at fourth order):
+ *   predict  xp = x + v h + a h^2/2 + j h^3/6,   vp = v + a h + j h^2/2
+ *   evaluate a1, j1 at (xp, vp)
+ *   correct  v1 = v + (a + a1) h/2 + (j - j1) h^2/12
+ *            x1 = x + (v + v1) h/2 + (a - a1) h^2/12
+ * acc/jerk hold a(x0), j(x0) on entry when valid != 0 and a1, j1 on exit.
+ */
+void orc_hermite4(int64_t N, double *pos, double *vel, const double *mass, double eps, double G,
+                  double h, int64_t nsteps, int valid, double *acc, double *jerk) {
+    if (!valid) orc_forces_jerk(N, pos, vel, mass, eps, G, acc, jerk, 0);
+    double *xp = (double *)malloc(sizeof(double) * 3 * N);
+    double *vp = (double *)malloc(sizeof(double) * 3 * N);
+    double *a1 = (double *)malloc(sizeof(double) * 3 * N);
+    double *j1 = (double *)malloc(sizeof(double) * 3 * N);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        for (int64_t k = 0; k < 3 * N; ++k) {
+            xp[k] = pos[k] + vel[k] * h + acc[k] * h * h / 2.0 + jerk[k] * h * h * h / 6.0;
+            vp[k] = vel[k] + acc[k] * h + jerk[k] * h * h / 2.0;
+        }
+        orc_forces_jerk(N, xp, vp, mass, eps, G, a1, j1, 0);
+        for (int64_t k = 0; k < 3 * N; ++k) {
+            const double v1 = vel[k] + (acc[k] + a1[k]) * h / 2.0 + (jerk[k] - j1[k]) * h * h / 12.0;
+            pos[k] = pos[k] + (vel[k] + v1) * h / 2.0 + (acc[k] - a1[k]) * h * h / 12.0;
+            vel[k] = v1;
+            acc[k] = a1[k];
+            jerk[k] = j1[k];
+        }
+    }
+    free(xp);
+    free(vp);
+    free(a1);
+    free(j1);
+}
+
+/* orc_forces_jerk restricted to the rows listed in `rows` (each against all N). */
+void orc_forces_jerk_rows(int64_t N, const double *pos, const double *vel, const double *mass,
+                          double eps, double G, int64_t nrows, const int64_t *rows, double *acc,
+                          double *jerk) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        double a[3] = {0, 0, 0}, jk[3] = {0, 0, 0};
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double d[3], w[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = pos[3 * j + c] - pos[3 * i + c];
+                w[c] = vel[3 * j + c] - vel[3 * i + c];
+            }
+            const double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+            if (s2 == 0.0) continue;
+            const double s = sqrt(s2);
+            const double inv3 = 1.0 / (s2 * s);
+            const double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+            for (int c = 0; c < 3; ++c) {
+                a[c] += mass[j] * d[c] * inv3;
+                jk[c] += mass[j] * (w[c] * inv3 - 3.0 * dw * d[c] * inv3 / s2);
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            acc[3 * r + c] = G * a[c];
+            jerk[3 * r + c] = G * jk[c];
+        }
     }
 }

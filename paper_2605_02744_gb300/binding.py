@@ -39,7 +39,7 @@ POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
-            "nb_forces_noalloc", "nb_launch_count")
+            "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4")
 
 
 class NbError(RuntimeError):
@@ -99,6 +99,9 @@ _SIGS = {
                                            _vp, _vp, _sz, _OPTS]),
     "nb_poll_status": (ctypes.c_int, [_vp, _sz, _vp]),
     "nb_forces_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _OPTS]),
+    "nb_forces_jerk": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _sz, _OPTS]),
+    "nb_hermite4": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _vp, _vp, _i32, _d, _i64, _vp, _sz,
+                                   _OPTS]),
 }
 
 
@@ -268,6 +271,27 @@ def nb_step_vjp_reverse(pos, vhalf, acc, mass, eps: float, rewind_kick: float,
         float(drift_dt), float(kick_coef), _dptr(pos_bar, "pos_bar", f64),
         _dptr(vel_bar, "vel_bar", f64), _dptr(mass_bar, "mass_bar", f64), _dptr(ws, "ws"),
         ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_forces_jerk(pos, vel, mass, eps: float, acc, jerk, pot, ws, opts: nb_opts):
+    import torch
+    f64 = torch.float64
+    n = mass.shape[0]
+    _check(lib().nb_forces_jerk(
+        _dptr(pos, "pos", f64), _dptr(vel, "vel", f64), _dptr(mass, "mass", f64), n, float(eps),
+        _dptr(acc, "acc", f64), _dptr(jerk, "jerk", f64), _dptr(pot, "pot", f64, True),
+        _dptr(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_hermite4(pos, vel, mass, eps: float, acc, jerk, acc_valid: bool, dt: float, nsteps: int,
+                ws, opts: nb_opts):
+    import torch
+    f64 = torch.float64
+    n = mass.shape[0]
+    _check(lib().nb_hermite4(
+        _dptr(pos, "pos", f64), _dptr(vel, "vel", f64), _dptr(mass, "mass", f64), n, float(eps),
+        _dptr(acc, "acc", f64), _dptr(jerk, "jerk", f64), int(bool(acc_valid)), float(dt),
+        int(nsteps), _dptr(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(opts)))
 
 
 def nb_poll_status(ws, opts: nb_opts | None = None) -> int:

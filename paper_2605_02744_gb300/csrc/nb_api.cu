@@ -568,6 +568,65 @@ int nb_step_vjp_reverse(double *pos, double *vhalf, double *acc, const double *m
     return launch_vjp(j);
 }
 
+static int make_jerk_job(JerkJob *j, double *pos, double *vel, const double *mass, int64_t N,
+                         double eps, double *acc, double *jerk, double *pot, void *ws,
+                         size_t ws_bytes, const nb_opts *o) {
+    memset(j, 0, sizeof *j);
+    NB_TRY(check_common(o, N, eps));
+    NB_TRY(check_ptr(pos, "pos"));
+    NB_TRY(check_ptr(vel, "vel"));
+    NB_TRY(check_ptr(mass, "mass"));
+    NB_TRY(check_ptr(acc, "acc"));
+    NB_TRY(check_ptr(jerk, "jerk"));
+    NB_TRY(check_ptr(pot, "pot", true));
+    j->L = ws_layout(N, 1, o);
+    NB_TRY(check_ws(ws, ws_bytes, j->L));
+    j->pos = pos;
+    j->vel = vel;
+    j->mass = mass;
+    j->N = N;
+    j->eps = eps;
+    j->G = o->G;
+    j->acc = acc;
+    j->jerk = jerk;
+    j->pot = pot;
+    j->precision = o->precision;
+    j->timeout = timeout_of(o);
+    j->stream = (cudaStream_t)o->stream;
+    j->ws = (char *)ws;
+    return NB_OK;
+}
+
+int nb_forces_jerk(const double *pos, const double *vel, const double *mass, int64_t N,
+                   double eps, double *acc, double *jerk, double *pot, void *ws, size_t ws_bytes,
+                   const nb_opts *o) {
+    clear_error();
+    JerkJob j;
+    NB_TRY(make_jerk_job(&j, const_cast<double *>(pos), const_cast<double *>(vel), mass, N, eps,
+                         acc, jerk, pot, ws, ws_bytes, o));
+    j.nsteps = 0;
+    return launch_jerk(j);
+}
+
+int nb_hermite4(double *pos, double *vel, const double *mass, int64_t N, double eps, double *acc,
+                double *jerk, int32_t acc_valid, double dt, int64_t nsteps, void *ws,
+                size_t ws_bytes, const nb_opts *o) {
+    clear_error();
+    if (!isfinite(dt)) return fail(NB_ERR_INVALID, "dt must be finite");
+    if (nsteps < 0) return fail(NB_ERR_INVALID, "nsteps must be >= 0");
+    JerkJob j;
+    NB_TRY(make_jerk_job(&j, pos, vel, mass, N, eps, acc, jerk, nullptr, ws, ws_bytes, o));
+    if (!acc_valid) {
+        JerkJob e = j;
+        e.nsteps = 0;
+        NB_TRY(launch_jerk(e));
+    }
+    if (nsteps == 0) return NB_OK;
+    j.h = dt;
+    j.nsteps = nsteps;
+    return launch_jerk(j);
+}
+
 int nb_poll_status(void *ws, size_t ws_bytes, void *stream) {
     clear_error();
     if (!ws || ws_bytes < 256) return fail(NB_ERR_INVALID, "workspace NULL or too small");

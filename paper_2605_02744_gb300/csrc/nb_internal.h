@@ -206,6 +206,26 @@ int launch_kick_drift_pack(double *pos, double *vel, const double *acc, const do
 int launch_energy(const double *vel, const double *mass, const double *pot, int64_t N,
                   double *out3, char *ws, const WsLayout &L, cudaStream_t st);
 
+struct JerkJob {
+    double *pos;
+    double *vel;
+    const double *mass;
+    int64_t N;
+    double eps;
+    double G;
+    double *acc;
+    double *jerk;
+    double *pot;
+    double h;
+    int64_t nsteps;  // 0 = evaluate a, jerk, phi at the current state
+    int precision;
+    long long timeout;
+    cudaStream_t stream;
+    char *ws;
+    WsLayout L;
+};
+int launch_jerk(const JerkJob &job);
+
 struct BatchedJob {
     const double *mass;
     const int64_t *offsets;
