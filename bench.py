@@ -49,6 +49,21 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, device):
+    """Max of a per-rank number over all ranks of the process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, steps: int, interactions_per_step: float, max_ms: float) -> float:
+    """Whole-job rate: every rank's interactions over the slowest rank's time
+    (replicas, weak scaling), in G interactions/s."""
+    return world * steps * interactions_per_step / (max_ms * 1e-3) / 1e9
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -362,12 +377,10 @@ def run_ours(args):
     times, clocks, kahan_launches = results["kahan"]
     total_ms = sum(times)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
         torch.distributed.barrier()
     inter = float(N_MAIN) * N_MAIN
-    value = ws * args.steps * inter / (total_ms * 1e-3) / 1e9
+    value = aggregate_rate(ws, args.steps, inter, total_ms)
 
     # end to end through the public API from pinned host buffers
     host = {k: torch.as_tensor(getattr(s, k)).pin_memory() for k in ("pos", "vel", "mass")}

@@ -65,30 +65,52 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    """Declares the C signatures on a loaded oracle library."""
+    lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+    lib.orc_forces.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp,
+                               _dp]
+    lib.orc_forces_rows.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int64, _i64p, _dp, _dp]
+    lib.orc_kdk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_int64, ctypes.c_int, _dp, _dp]
+    lib.orc_energy.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp]
+    lib.orc_forces_vjp.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                   _dp, _dp, _dp, _dp]
+    lib.orc_forces_jerk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                    ctypes.c_double, _dp, _dp, _dp]
+    lib.orc_forces_jerk_rows.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int64, _i64p, _dp, _dp]
+    lib.orc_hermite4.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                 _dp, _dp]
+    return lib
+
+
+def use_library(path):
+    """Swaps the oracle to another build of nbody_oracle.c (the mutation
+    tests plant mistakes in a copy to show the pins catch them); returns the
+    previous library so the caller can restore it with ``restore_library``."""
+    global _lib
+    with _lock:
+        prev = _lib
+        _lib = _configure(ctypes.CDLL(path))
+    return prev
+
+
+def restore_library(prev):
+    global _lib
+    with _lock:
+        _lib = prev
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            lib.orc_num_threads.restype = ctypes.c_int
-            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
-            lib.orc_forces.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
-                                       ctypes.c_double, _dp, _dp]
-            lib.orc_forces_rows.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
-                                            ctypes.c_double, ctypes.c_int64, _i64p, _dp, _dp]
-            lib.orc_kdk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64,
-                                    ctypes.c_int, _dp, _dp]
-            lib.orc_energy.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp]
-            lib.orc_forces_vjp.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
-                                           ctypes.c_double, _dp, _dp, _dp, _dp]
-            lib.orc_forces_jerk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
-                                            ctypes.c_double, _dp, _dp, _dp]
-            lib.orc_forces_jerk_rows.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
-                                                 ctypes.c_double, ctypes.c_int64, _i64p, _dp, _dp]
-            lib.orc_hermite4.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, ctypes.c_int64,
-                                         ctypes.c_int, _dp, _dp]
+            _configure(lib)
             _lib = lib
     return _lib
 

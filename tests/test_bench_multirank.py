@@ -1,0 +1,61 @@
+"""The benchmark's multi-rank host logic on CPU with gloo, world size 2:
+max-over-ranks timing, the replicas' whole-job rate, and the reference arm
+printing only on rank 0."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = bench.max_over_ranks(100.0 + 50.0 * rank, "cpu")
+        rate = bench.aggregate_rate(world, 5, 1e12, m)
+        dist.barrier()
+        out.put((rank, m, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_aggregate_rate_gloo():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [150.0, 150.0]
+    # 2 ranks x 5 steps x 1e12 interactions in 0.15 s = 66666.7 G/s
+    assert all(abs(r[2] - 2 * 5 * 1e12 / 0.15 / 1e9) < 1e-6 for r in res)
+
+
+def test_reference_arm_is_silent_on_other_ranks(capsys, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup = 1, 3
+    assert bench.run_reference(A()) == 0
+    assert capsys.readouterr().out == ""
