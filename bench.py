@@ -459,7 +459,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "force_sk_kernel<256,4,256,3,KAHAN,split,adaptive>",
+                     "kernel": "force_sk_kernel<512,2,1024,2,KAHAN,split,adaptive>",
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{max_mhz:.0f} MHz (max SM clock)",

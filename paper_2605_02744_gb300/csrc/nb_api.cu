@@ -54,14 +54,16 @@ bool shape_compiled(const Shape &s, int kind) {
     return kind == kKindForce ? force_shape_compiled(s) : vjp_shape_compiled(s);
 }
 
-// Built-in shapes, from an autotuner sweep on GB300 (Kahan / F64ACC, split
-// positions): (256 threads, 4 i/thread, 256-j tiles, 3 stages) is fastest
-// from N = 65536 up; (256, 2, 256, 3) at N = 16384; (128, 1, 64, 2) at 1024.
-// CTAs per SM are clamped by register occupancy (one 256-thread CTA).
+// Built-in shapes, from autotuner sweeps on GB300 (Kahan / F64ACC, default
+// positions): 512 threads x 2 i/thread with 1024-particle tiles from
+// N = 2^18 (the adaptive path; 2^20: 449 ms vs 538 ms for 256 x 4 x 256,
+// because two i per thread leave room for 16 resident warps per SM);
+// 256 x 2 x 512 from 2^15; 256 x 2 x 256 from 2^12; 128 x 1 x 64 below.
 Shape default_shape(int64_t N, int precision, int kind) {
     (void)precision;
     if (kind == kKindForce) {
-        if (N >= (1 << 15)) return Shape{256, 4, 256, 3, 2};
+        if (N >= (1 << 18)) return Shape{512, 2, 1024, 2, 1};
+        if (N >= (1 << 15)) return Shape{256, 2, 512, 2, 2};
         if (N >= (1 << 12)) return Shape{256, 2, 256, 3, 2};
         return Shape{128, 1, 64, 2, 4};
     }

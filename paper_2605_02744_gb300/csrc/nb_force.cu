@@ -397,8 +397,11 @@ __global__ void __launch_bounds__(NT)
 // ---------------------------------------------------------- dispatch
 // Shapes compiled into this build: (threads, i per thread, tile_j, stages).
 #define NB_FORCE_SHAPES(X) \
-    X(256, 4, 256, 3)      \
+    X(512, 2, 1024, 2)     \
+    X(512, 2, 512, 2)      \
+    X(256, 2, 512, 2)      \
     X(256, 2, 256, 3)      \
+    X(256, 4, 256, 3)      \
     X(128, 2, 128, 3)      \
     X(128, 1, 64, 2)
 
@@ -414,6 +417,11 @@ template <int NT, int IR, int TJ, int ST, int POL, bool GUARD, bool SPLIT, bool 
 static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
     auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT, NF>;
     const size_t smem = (size_t)ST * (SPLIT ? 7 : 4) * 4 * TJ + (size_t)ST * 8;
+    // stages above 48 KB need the opt-in (up to 227 KB per CTA)
+    static const int optin = smem > 48 * 1024
+        ? (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+        : 0;
+    (void)optin;
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);

@@ -24,7 +24,8 @@ _lock = threading.Lock()
 
 FORCE_CANDIDATES = [
     dict(threads=t, i_per_thread=i, tile_j=j, stages=s, ctas_per_sm=c)
-    for (t, i, j, s) in [(256, 4, 256, 3), (256, 2, 256, 3), (128, 2, 128, 3), (128, 1, 64, 2)]
+    for (t, i, j, s) in [(512, 2, 1024, 2), (512, 2, 512, 2), (256, 2, 512, 2), (256, 2, 256, 3),
+                         (256, 4, 256, 3), (128, 2, 128, 3), (128, 1, 64, 2)]
     for c in (1, 2, 4)
 ]
 BATCHED_CANDIDATES = [dict(cluster_ctas=c) for c in (2, 4, 8)]

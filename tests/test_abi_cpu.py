@@ -63,6 +63,7 @@ def test_workspace_sizes(B):
 
 def test_tune_validation(B):
     assert B.nb_tune_valid({"threads": 256, "i_per_thread": 4, "tile_j": 256, "stages": 3})
+    assert B.nb_tune_valid({"threads": 512, "i_per_thread": 2, "tile_j": 1024, "stages": 2})
     assert B.nb_tune_valid({"threads": 128, "i_per_thread": 1, "tile_j": 64, "stages": 2})
     assert not B.nb_tune_valid({"threads": 96, "i_per_thread": 4, "tile_j": 256, "stages": 3})
     assert not B.nb_tune_valid({"threads": 256, "i_per_thread": 4, "tile_j": 256, "stages": 3,

@@ -78,7 +78,8 @@ def test_hand_worked_two_body_on_gpu():
     np.testing.assert_allclose(host(p), [-0.4, -0.2], rtol=1e-15)
 
 
-@pytest.mark.parametrize("shape", [(256, 4, 256, 3), (256, 2, 256, 3), (128, 2, 128, 3),
+@pytest.mark.parametrize("shape", [(512, 2, 1024, 2), (512, 2, 512, 2), (256, 2, 512, 2),
+                                   (256, 2, 256, 3), (256, 4, 256, 3), (128, 2, 128, 3),
                                    (128, 1, 64, 2)])
 @pytest.mark.parametrize("cps", [1, 2, 4])
 def test_every_compiled_shape(shape, cps):
@@ -88,6 +89,13 @@ def test_every_compiled_shape(shape, cps):
     s = ics.plummer(6000, seed=11)
     _check(s, 0.01, "f64acc", tune=t)
     _check(s, 0.01, "kahan", tune=t)
+    # the adaptive (Morton-sorted) path in the same shape
+    o = binding.make_opts("kahan", tune=t, positions="adaptive")
+    acc = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    ws = binding.workspace(s.n, 1, o)
+    binding.nb_forces(dev(s.pos), dev(s.mass), 0.01, acc, None, ws, o)
+    ra, _ = oracle.forces(s.pos, s.mass, 0.01)
+    assert rel_vec_err(host(acc), ra).max() <= 1e-5
 
 
 def test_gravitational_constant():
