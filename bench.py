@@ -507,6 +507,25 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_batched(args):
+    """--profile-batched B: the batched kernel on the first B clusters of the
+    512-cluster workload, 20 KDK steps (the case its ncu capture used)."""
+    import numpy as np
+    import torch
+
+    import paper_2605_02744_gb300 as pkg
+    from paper_2605_02744_gb300 import api, ics
+    pkg.build()
+    sizes = ics.batched_sizes()[: args.profile_batched]
+    s = ics.batched_plummer(b=len(sizes), seed=1, sizes=sizes)
+    for _ in range(args.warmup + args.steps):
+        g = api.System(s.pos, s.vel, s.mass, np.full(len(sizes), 0.01), offsets=s.offsets,
+                       precision="f64acc", tune={"cluster_ctas": 4, "threads": 512})
+        g.step(1e-3, 20)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,12 +540,16 @@ def main():
     ap.add_argument("--profile", type=int, default=0,
                     help="run only nb_forces on a Plummer sphere of this size (for ncu)")
     ap.add_argument("--precision", default="kahan")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="run only the batched kernel on this many clusters (for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile_case(args)
+    if args.profile_batched:
+        return run_profile_batched(args)
     return run_ours(args)
 
 

@@ -88,7 +88,7 @@ typedef enum {
  * defaults for the problem size; nb_tune_valid() reports whether a shape
  * is one this build was compiled for. */
 typedef struct nb_tune {
-    int32_t threads;      /* threads per CTA: 128 or 256                   */
+    int32_t threads;      /* threads per CTA: 128..1024 (batched: 256/512) */
     int32_t i_per_thread; /* i-particles held in registers per thread: 1,2,4,8 */
     int32_t tile_j;       /* j-particles per shared-memory stage: 64..512   */
     int32_t stages;       /* depth of the bulk-copy ring: 2..4               */

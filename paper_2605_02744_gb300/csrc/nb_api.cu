@@ -319,6 +319,7 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.acc_valid = false;
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
+    j.threads = o->tune ? o->tune->threads : 0;
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)ws;
@@ -344,6 +345,7 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
     j.acc_valid = s->acc_valid != 0;
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
+    j.threads = o->tune ? o->tune->threads : 0;
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)s->ws;

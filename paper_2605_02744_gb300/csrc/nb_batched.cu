@@ -16,11 +16,12 @@
 //
 // The packed positions are double-buffered (one barrier per step).  j-tiles
 // are read through L2 (ld.global.cg: other CTAs of the cluster wrote them) into
-// shared memory.  Each thread keeps 2 (slices of >= 1024 particles: 4)
-// i-particles in registers for independent FMA chains; when a slice has
-// fewer than two particles per thread, groups of L = 2..32 lanes share the
-// same i-particles, split the j-pairs, and are summed with a fixed
-// xor-shuffle tree (bitwise reproducible).
+// shared memory, the next tile prefetched into registers during the current
+// one.  Each thread keeps 2 i-particles in registers (independent FMA chains,
+// <= 128 registers so a 512-thread CTA fits); when a slice has fewer than
+// two particles per thread, groups of L = 2..32 lanes share the same
+// i-particles, split the j-pairs, and are summed with a fixed xor-shuffle
+// tree (bitwise reproducible).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -37,8 +38,7 @@ using dev::Acc;
 using dev::f2;
 using dev::pair2;
 
-constexpr int kBT = 256;       // threads per CTA
-constexpr int kBTJ = 256;      // j-particles per shared-memory tile
+constexpr int kBTJ = 512;      // j-particles per shared-memory tile
 constexpr int kBMaxN = 8192;   // particles per cluster (device-checked)
 constexpr int kBSortMax = 8192;
 constexpr int kBMaxSlots = 4096;
@@ -127,7 +127,7 @@ __global__ void batched_setup_kernel(const int64_t *__restrict__ offsets, int B,
 __device__ __forceinline__ void pack_slice(const BatchedParams &p, int64_t s0, int64_t s1,
                                            float *pk, bool kick_drift) {
     const double half = 0.5 * p.dt;
-    for (int64_t i = s0 + threadIdx.x; i < s1; i += kBT) {
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
         float hi[3], lo[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -146,16 +146,19 @@ __device__ __forceinline__ void pack_slice(const BatchedParams &p, int64_t s0, i
 }
 
 // Forces on the i of one chunk of the slice [.., s1) from all j of the
-// system [o0, o1).  The CTA's threads form G = kBT / L groups of L lanes; the
+// system [o0, o1).  The CTA's BT threads form G = BT / L groups of L lanes;
 // group g holds the IR particles c0 + k G + g (k < IR) and its lanes split
-// the j-pairs of every tile (lane l takes pairs l, l + L, ...).
-template <int IR, int POL>
+// the j-pairs of every tile (lane l takes pairs l, l + L, ...).  The next
+// tile is loaded into registers while the current one is computed.
+template <int BT, int IR, int POL>
 __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, int64_t o1,
                                             int64_t c0, int64_t s1, const float *pk, float eps2,
                                             double kick, int L, float (&tile)[7][kBTJ]) {
+    constexpr int PER = 7 * kBTJ / BT;  // tile floats each thread stages
+    static_assert(7 * kBTJ % BT == 0, "tile must split evenly over the CTA");
     const int tid = threadIdx.x;
     const int lane = tid % L;
-    const int G = kBT / L;
+    const int G = BT / L;
     const int grp = tid / L;
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR];
     float mi[IR];
@@ -180,13 +183,27 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
         for (int e = 0; e < 4; ++e) tot[k][e].zero();
     }
     const float2 e2 = f2(eps2, eps2);
+    float pre[PER];
+    auto fetch = [&](int64_t jt0) {
+        const int64_t nj = (o1 - jt0) < kBTJ ? (o1 - jt0) : kBTJ;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = tid + r * BT;
+            const int arr = e / kBTJ, jj = e % kBTJ;
+            pre[r] = jj < nj ? __ldcg(pk + arr * p.Np + jt0 + jj) : 0.f;
+        }
+    };
+    fetch(o0);
     for (int64_t jt0 = o0; jt0 < o1; jt0 += kBTJ) {
         const int nj = (int)((o1 - jt0) < kBTJ ? (o1 - jt0) : kBTJ);
-        for (int e = tid; e < 7 * kBTJ; e += kBT) {
-            const int arr = e / kBTJ, jj = e % kBTJ;
-            tile[arr][jj] = jj < nj ? __ldcg(pk + arr * p.Np + jt0 + jj) : 0.f;
+        __syncthreads();  // the previous tile is no longer read
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = tid + r * BT;
+            tile[e / kBTJ][e % kBTJ] = pre[r];
         }
         __syncthreads();
+        if (jt0 + kBTJ < o1) fetch(jt0 + kBTJ);  // in flight during the pairs below
         float2 ax[IR], ay[IR], az[IR], ph[IR];
 #pragma unroll
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
@@ -209,7 +226,6 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
             tot[k][2].add(az[k].x + az[k].y);
             tot[k][3].add(ph[k].x + ph[k].y);
         }
-        __syncthreads();
     }
     double v[IR][4];
 #pragma unroll
@@ -242,32 +258,26 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
     if (bad) dev::set_status(p.status, kStatusNonFinite);
 }
 
-// Chooses i-particles per group (IR) and lanes per group (L) for a slice:
-// at least IR independent chains per thread, and as many lanes per group as
-// the slice leaves room for, so small slices still fill the CTA.
-template <int POL>
+// Two i-particles per group (independent FMA chains) and as many lanes per
+// group as the slice leaves room for, so small slices still fill the CTA.
+template <int BT, int POL>
 __device__ __forceinline__ void force_slice(const BatchedParams &p, int64_t o0, int64_t o1,
                                             int64_t s0, int64_t s1, const float *pk, float eps2,
                                             double kick, float (&tile)[7][kBTJ]) {
     const int64_t ns = s1 - s0;
-    if (ns >= (int64_t)kBT * 4) {
-        for (int64_t c0 = s0; c0 < s1; c0 += (int64_t)kBT * 4)
-            force_chunk<4, POL>(p, o0, o1, c0, s1, pk, eps2, kick, 1, tile);
-    } else {
-        const int64_t groups = (ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1;  // IR = 2
-        int L = 1;
-        while (L < 32 && (int64_t)(2 * L) * groups <= kBT) L <<= 1;
-        const int64_t chunk = (int64_t)(kBT / L) * 2;
-        for (int64_t c0 = s0; c0 < s1; c0 += chunk)
-            force_chunk<2, POL>(p, o0, o1, c0, s1, pk, eps2, kick, L, tile);
-    }
+    const int64_t groups = (ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1;
+    int L = 1;
+    while (L < 32 && (int64_t)(2 * L) * groups <= BT) L <<= 1;
+    const int64_t chunk = (int64_t)(BT / L) * 2;
+    for (int64_t c0 = s0; c0 < s1; c0 += chunk)
+        force_chunk<BT, 2, POL>(p, o0, o1, c0, s1, pk, eps2, kick, L, tile);
     // the epilogue's acc/vel writes (lane 0 of each group) are read by other
     // threads of this CTA in the next kick-drift-pack
     __syncthreads();
 }
 
-template <int CS, int POL>
-__global__ void __launch_bounds__(kBT) batched_kernel(const BatchedParams p) {
+template <int CS, int BT, int POL>
+__global__ void __launch_bounds__(BT, 1) batched_kernel(const BatchedParams p) {
     __shared__ __align__(16) float tile[7][kBTJ];
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank();
@@ -291,14 +301,14 @@ __global__ void __launch_bounds__(kBT) batched_kernel(const BatchedParams p) {
             if (!p.acc_valid) {
                 pack_slice(p, s0, s1, p.pack0, false);
                 cl.sync();
-                force_slice<POL>(p, o0, o1, s0, s1, p.pack0, eps2, 0.0, tile);
+                force_slice<BT, POL>(p, o0, o1, s0, s1, p.pack0, eps2, 0.0, tile);
             }
             for (int64_t step = 0; step < p.nsteps; ++step) {
                 buf ^= 1;
                 float *pk = buf ? p.pack1 : p.pack0;
                 pack_slice(p, s0, s1, pk, true);
                 cl.sync();
-                force_slice<POL>(p, o0, o1, s0, s1, pk, eps2, 0.5 * p.dt, tile);
+                force_slice<BT, POL>(p, o0, o1, s0, s1, pk, eps2, 0.5 * p.dt, tile);
             }
         }
         cl.sync();
@@ -306,16 +316,16 @@ __global__ void __launch_bounds__(kBT) batched_kernel(const BatchedParams p) {
 }
 
 // ---------------------------------------------------------------- launch
-template <int CS, int POL>
+template <int CS, int BT, int POL>
 static int launch_batched_cs(const BatchedParams &p, cudaStream_t st) {
-    auto kern = batched_kernel<CS, POL>;
+    auto kern = batched_kernel<CS, BT, POL>;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CS;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kBT, 1, 1);
+    cfg.blockDim = dim3(BT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cfg.attrs = attr;
@@ -344,13 +354,18 @@ static int launch_batched_cs(const BatchedParams &p, cudaStream_t st) {
 }
 
 template <int POL>
-static int launch_batched_pol(const BatchedParams &p, int cs, cudaStream_t st) {
-    switch (cs) {
-        case 2: return launch_batched_cs<2, POL>(p, st);
-        case 4: return launch_batched_cs<4, POL>(p, st);
-        case 8: return launch_batched_cs<8, POL>(p, st);
+static int launch_batched_pol(const BatchedParams &p, int cs, int bt, cudaStream_t st) {
+    switch (cs * 10000 + bt) {
+        case 2 * 10000 + 256: return launch_batched_cs<2, 256, POL>(p, st);
+        case 4 * 10000 + 256: return launch_batched_cs<4, 256, POL>(p, st);
+        case 8 * 10000 + 256: return launch_batched_cs<8, 256, POL>(p, st);
+        case 2 * 10000 + 512: return launch_batched_cs<2, 512, POL>(p, st);
+        case 4 * 10000 + 512: return launch_batched_cs<4, 512, POL>(p, st);
+        case 8 * 10000 + 512: return launch_batched_cs<8, 512, POL>(p, st);
     }
-    return fail(NB_ERR_UNSUPPORTED, "batched cluster size %d not compiled (2, 4, 8)", cs);
+    return fail(NB_ERR_UNSUPPORTED,
+                "batched shape (%d CTAs per cluster, %d threads) not compiled (2/4/8 x 256/512)",
+                cs, bt);
 }
 
 int launch_batched(const BatchedJob &j) {
@@ -395,10 +410,11 @@ int launch_batched(const BatchedJob &j) {
         NB_CUDA(cudaGetLastError());
     }
     const int cs = j.cluster > 0 ? j.cluster : 8;
+    const int bt = j.threads > 0 ? j.threads : 512;
     switch (j.precision) {
-        case NB_PREC_FP32: return launch_batched_pol<NB_PREC_FP32>(p, cs, j.stream);
-        case NB_PREC_KAHAN: return launch_batched_pol<NB_PREC_KAHAN>(p, cs, j.stream);
-        case NB_PREC_F64ACC: return launch_batched_pol<NB_PREC_F64ACC>(p, cs, j.stream);
+        case NB_PREC_FP32: return launch_batched_pol<NB_PREC_FP32>(p, cs, bt, j.stream);
+        case NB_PREC_KAHAN: return launch_batched_pol<NB_PREC_KAHAN>(p, cs, bt, j.stream);
+        case NB_PREC_F64ACC: return launch_batched_pol<NB_PREC_F64ACC>(p, cs, bt, j.stream);
     }
     return fail(NB_ERR_INVALID, "unknown precision %d", j.precision);
 }

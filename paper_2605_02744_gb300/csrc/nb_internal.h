@@ -242,6 +242,7 @@ struct BatchedJob {
     bool acc_valid;
     int precision;
     int cluster;      // CTAs per thread-block cluster (0 = default)
+    int threads;      // threads per CTA (0 = default)
     long long timeout;
     cudaStream_t stream;
     char *ws;

@@ -28,7 +28,7 @@ FORCE_CANDIDATES = [
                          (256, 4, 256, 3), (128, 2, 128, 3), (128, 1, 64, 2)]
     for c in (1, 2, 4)
 ]
-BATCHED_CANDIDATES = [dict(cluster_ctas=c) for c in (2, 4, 8)]
+BATCHED_CANDIDATES = [dict(cluster_ctas=c, threads=t) for c in (4, 8) for t in (256, 512)]
 VJP_CANDIDATES = [
     dict(threads=t, i_per_thread=i, tile_j=j, stages=s, ctas_per_sm=4)
     for (t, i, j, s) in [(128, 2, 128, 3), (256, 2, 128, 3), (256, 1, 128, 3), (128, 1, 64, 2)]

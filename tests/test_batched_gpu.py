@@ -38,10 +38,11 @@ def _eps(b, seed=0):
 
 @pytest.mark.parametrize("prec", ["f64acc", "kahan"])
 @pytest.mark.parametrize("cs", [2, 4, 8])
-def test_forces_batched_per_cluster(prec, cs):
+@pytest.mark.parametrize("bt", [256, 512])
+def test_forces_batched_per_cluster(prec, cs, bt):
     s = _batch(SIZES)
     eps = _eps(len(SIZES))
-    opts = binding.make_opts(prec, tune={"cluster_ctas": cs})
+    opts = binding.make_opts(prec, tune={"cluster_ctas": cs, "threads": bt})
     n = s.n
     acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     pot = torch.empty(n, dtype=torch.float64, device="cuda")
