@@ -409,7 +409,7 @@ int launch_batched(const BatchedJob &j) {
         count_launch();
         NB_CUDA(cudaGetLastError());
     }
-    const int cs = j.cluster > 0 ? j.cluster : 8;
+    const int cs = j.cluster > 0 ? j.cluster : 4;  // measured best on GB300 (4 x 512 threads)
     const int bt = j.threads > 0 ? j.threads : 512;
     switch (j.precision) {
         case NB_PREC_FP32: return launch_batched_pol<NB_PREC_FP32>(p, cs, bt, j.stream);

@@ -100,3 +100,24 @@ def test_kepler_circular_orbit_eps0():
     x, v, _, _ = oracle.kdk(pos, vel, m, 0.0, 2 * math.pi / n, n)
     assert np.abs(host(g.pos) - x).max() < 1e-12
     assert np.abs(host(g.pos) - pos).max() < 5e-4  # one period closes to O(h^2)
+
+
+def test_lognormal_65536_ten_steps_three_variants():
+    # the 65536-particle log-normal workload: 10 KDK steps of dt = 1e-4 with
+    # FP64 accumulation, FP32 accumulation and FP64 pairs against the
+    # oracle's 10 steps (positions, velocities, accelerations)
+    s = ics.plummer_lognormal(65536, seed=0)
+    eps, h, n = 1e-3, 1e-4, 10
+    xo, vo, ao, _ = oracle.kdk(s.pos, s.vel, s.mass, eps, h, n)
+    dx = np.abs(xo - s.pos).max()
+    dv = np.abs(vo - s.vel).max()
+    for prec, tol in (("f64acc", 1e-5), ("fp64", 1e-11), ("fp32", None)):
+        g = api.System(s.pos, s.vel, s.mass, eps, precision=prec)
+        g.step(h, n)
+        assert g.poll() == binding.NB_OK
+        ex = np.abs(host(g.pos) - xo).max() / dx
+        ev = np.abs(host(g.vel) - vo).max() / dv
+        if tol is not None:
+            assert ex <= tol and ev <= tol, (prec, ex, ev)
+            from tests.gpu_util import rel_vec_err
+            assert rel_vec_err(host(g.acc), ao).max() <= max(tol, 1e-12), prec
