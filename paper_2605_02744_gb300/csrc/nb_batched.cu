@@ -207,17 +207,28 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
         float2 ax[IR], ay[IR], az[IR], ph[IR];
 #pragma unroll
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
-        const int npairs = (nj + 1) / 2;  // an odd tail pairs with a zero-mass pad
-        for (int jp = lane; jp < npairs; jp += L) {
-            const float2 X = *reinterpret_cast<const float2 *>(&tile[0][2 * jp]);
-            const float2 Y = *reinterpret_cast<const float2 *>(&tile[1][2 * jp]);
-            const float2 Z = *reinterpret_cast<const float2 *>(&tile[2][2 * jp]);
-            const float2 M = *reinterpret_cast<const float2 *>(&tile[3][2 * jp]);
-            const float2 XL = *reinterpret_cast<const float2 *>(&tile[4][2 * jp]);
-            const float2 YL = *reinterpret_cast<const float2 *>(&tile[5][2 * jp]);
-            const float2 ZL = *reinterpret_cast<const float2 *>(&tile[6][2 * jp]);
-            pair2<IR, false, true>(X, Y, Z, XL, YL, ZL, M, e2, nx, ny, nz, nxl, nyl, nzl, ax, ay, az,
-                                   ph);
+        // quads of j (float4 loads); a ragged tail reads the zero-mass pad
+        const int nquads = (nj + 3) / 4;
+        auto quad = [&](int jq) {
+            const float4 X = *reinterpret_cast<const float4 *>(&tile[0][4 * jq]);
+            const float4 Y = *reinterpret_cast<const float4 *>(&tile[1][4 * jq]);
+            const float4 Z = *reinterpret_cast<const float4 *>(&tile[2][4 * jq]);
+            const float4 M = *reinterpret_cast<const float4 *>(&tile[3][4 * jq]);
+            const float4 XL = *reinterpret_cast<const float4 *>(&tile[4][4 * jq]);
+            const float4 YL = *reinterpret_cast<const float4 *>(&tile[5][4 * jq]);
+            const float4 ZL = *reinterpret_cast<const float4 *>(&tile[6][4 * jq]);
+            pair2<IR, false, true>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(XL.x, XL.y),
+                                   f2(YL.x, YL.y), f2(ZL.x, ZL.y), f2(M.x, M.y), e2, nx, ny, nz,
+                                   nxl, nyl, nzl, ax, ay, az, ph);
+            pair2<IR, false, true>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(XL.z, XL.w),
+                                   f2(YL.z, YL.w), f2(ZL.z, ZL.w), f2(M.z, M.w), e2, nx, ny, nz,
+                                   nxl, nyl, nzl, ax, ay, az, ph);
+        };
+        if (L == 1) {
+#pragma unroll 2
+            for (int jq = 0; jq < nquads; ++jq) quad(jq);
+        } else {
+            for (int jq = lane; jq < nquads; jq += L) quad(jq);
         }
 #pragma unroll
         for (int k = 0; k < IR; ++k) {
