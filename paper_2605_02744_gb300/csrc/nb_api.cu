@@ -143,13 +143,17 @@ bool positions_split(const nb_opts *o) {
     return o->precision != NB_PREC_FP32;
 }
 
-constexpr int64_t kAdaptiveMinN = 1 << 18;  // below, the sort costs more than it saves
+// Default thresholds of the adaptive path: a single evaluation pays a full
+// Morton sort, a step loop sorts once per kResortEvery steps.
+constexpr int64_t kAdaptiveMinN = 1 << 18;
+constexpr int64_t kAdaptiveMinNStepping = 1 << 15;
 
-bool positions_adaptive(const nb_opts *o, int64_t N) {
+bool positions_adaptive(const nb_opts *o, int64_t N, bool stepping) {
     if (o->precision == NB_PREC_FP64) return false;
     if (o->positions == NB_POS_ADAPTIVE) return true;
     if (o->positions != NB_POS_DEFAULT) return false;
-    return o->precision != NB_PREC_FP32 && N >= kAdaptiveMinN;
+    return o->precision != NB_PREC_FP32 &&
+           N >= (stepping ? kAdaptiveMinNStepping : kAdaptiveMinN);
 }
 
 // ------------------------------------------------------------ checks
@@ -211,6 +215,7 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     j->precision = o->precision;
     j->split = positions_split(o);
     j->adaptive = positions_adaptive(o, N);
+    j->reuse_order = false;
     j->gamma = o->near_gamma > 0.f ? o->near_gamma : kNearFarGamma;
     j->packed_ready = false;
     j->timeout = timeout_of(o);
@@ -355,7 +360,12 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
 static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
     ForceJob j;
     NB_TRY(make_force_job(&j, s->pos, s->mass, s->N, s->eps, s->acc, s->pot, s->ws, s->ws_bytes, o));
-    if (!s->acc_valid) NB_TRY(launch_force(j));
+    j.adaptive = positions_adaptive(o, s->N, nsteps > 0);
+    int64_t sorted_at = -1;  // step index of the last full Morton sort
+    if (!s->acc_valid) {
+        NB_TRY(launch_force(j));
+        sorted_at = 0;
+    }
     float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
     for (int64_t n = 0; n < nsteps; ++n) {
         // the adaptive path packs in Morton order inside launch_force
@@ -363,6 +373,8 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
                                       j.adaptive ? nullptr : soa, j.stream));
         ForceJob k = j;
         k.packed_ready = !j.adaptive;
+        k.reuse_order = j.adaptive && sorted_at >= 0 && n + 1 - sorted_at < kResortEvery;
+        if (j.adaptive && !k.reuse_order) sorted_at = n + 1;
         k.vel = s->vel;
         k.kick = 0.5 * dt;
         NB_TRY(launch_force(k));

@@ -491,7 +491,8 @@ int launch_force(const ForceJob &j) {
     if (adaptive) {
         int rc = launch_sorted_pack(j.pos, j.mass, j.N, j.L.Np, soa, sort_perm(sb, j.L),
                                     sort_keys(sb), sort_box6(sb, j.L), sort_tile_boxes(sb, j.L),
-                                    64, sort_block_boxes(sb, j.L), 32 * sh0.ipt, j.stream);
+                                    64, sort_block_boxes(sb, j.L), 32 * sh0.ipt, j.reuse_order,
+                                    j.stream);
         if (rc) return rc;
     } else if (!j.packed_ready) {
         int rc = launch_pack(j.pos, j.mass, j.N, j.L.Np, soa, j.stream);

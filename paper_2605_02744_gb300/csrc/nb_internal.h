@@ -100,6 +100,7 @@ struct ForceJob {
     int precision;
     bool split;         // hi/lo displacement (nb_positions resolved)
     bool adaptive;      // Morton-sorted pack, hi/lo only for near tile pairs
+    bool reuse_order;   // adaptive: keep the previous call's Morton order
     float gamma;        // near/far threshold of the adaptive path
     bool packed_ready;  // packA already holds float positions of `pos`
     long long timeout;
@@ -114,7 +115,9 @@ bool positions_split(const nb_opts *opts);
 // true when the split displacement is applied only to near tile pairs of a
 // Morton-sorted pack (explicit NB_POS_ADAPTIVE, or the default from N >= 2^16
 // for the KAHAN and F64ACC policies; 1/64 is the default near_gamma).
-bool positions_adaptive(const nb_opts *opts, int64_t N);
+bool positions_adaptive(const nb_opts *opts, int64_t N, bool stepping = false);
+// Steps of one nb_step call between full re-sorts of the adaptive path.
+constexpr int64_t kResortEvery = 16;
 
 // Well-separated threshold of the adaptive path: a (warp, 64-particle
 // sub-tile) pair takes the single-float displacement when the gap between
@@ -144,9 +147,13 @@ inline size_t sortbuf_bytes(int64_t Np) {
     return 8 * (size_t)sort_keys_len(Np) + 4 * (size_t)Np + 32 * (size_t)(Np / 64 + 1) +
            32 * (size_t)(Np / 32 + 1) + 64;
 }
+// reuse_order: the keys already hold a Morton order of these N particles
+// (an earlier call of the same step loop); only the pack and the boxes are
+// redone from the current positions.
 int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
                        int *perm, unsigned long long *keys, long long *box6, float *tile_boxes,
-                       int tile_unit, float *block_boxes, int block_unit, cudaStream_t st);
+                       int tile_unit, float *block_boxes, int block_unit, bool reuse_order,
+                       cudaStream_t st);
 
 // Number of float arrays of Np entries in a packed position buffer.
 constexpr int kPackArrays = 7;

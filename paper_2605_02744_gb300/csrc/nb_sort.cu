@@ -229,9 +229,12 @@ int64_t sort_keys_len(int64_t N) {
 
 int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
                        int *perm, unsigned long long *keys, long long *box6, float *tile_boxes,
-                       int tile_unit, float *block_boxes, int block_unit, cudaStream_t st) {
+                       int tile_unit, float *block_boxes, int block_unit, bool reuse_order,
+                       cudaStream_t st) {
     const int64_t P = sort_keys_len(N);
     const int threads = 256;
+    if (reuse_order) goto pack;  // same particles as the last sorted call: keep its order
+    {
     bbox_init_kernel<<<1, 32, 0, st>>>(box6);
     count_launch();
     const int64_t gb = std::min<int64_t>(cdiv(N, threads), 1024);
@@ -252,6 +255,8 @@ int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t
         bitonic_smem_kernel<<<nchunks, 1024, 0, st>>>(keys, k, k);
         count_launch();
     }
+    }
+pack:
     pack_sorted_kernel<<<(unsigned)std::min<int64_t>(cdiv(Np, threads), 8192), threads, 0, st>>>(
         pos, mass, keys, N, Np, soa, perm);
     count_launch();

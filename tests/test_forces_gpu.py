@@ -179,3 +179,19 @@ def test_adaptive_step_matches_split_step():
     assert ea <= 2e-5, ea
     dx = np.abs(host(a.pos) - host(b.pos)).max()
     assert dx <= 1e-12, dx
+
+
+def test_adaptive_step_loop_reuses_order_across_resort():
+    # 40000 particles step with the adaptive path by default (a step loop
+    # re-sorts every 16 steps); 20 steps cross one re-sort and must track the
+    # split-everywhere run to FP32-pair accuracy
+    s = ics.plummer(40000, seed=12)
+    a = api.System(s.pos, s.vel, s.mass, 2e-3, precision="f64acc")
+    b = api.System(s.pos, s.vel, s.mass, 2e-3, precision="f64acc")
+    b.opts.positions = binding.NB_POS_SPLIT
+    a.step(1e-4, 20)
+    b.step(1e-4, 20)
+    assert a.poll() == binding.NB_OK
+    assert rel_vec_err(host(a.acc), host(b.acc)).max() <= 2e-5
+    dx = np.abs(host(b.pos) - s.pos).max()
+    assert np.abs(host(a.pos) - host(b.pos)).max() <= 1e-6 * dx
