@@ -84,7 +84,8 @@ class System:
     """
 
     def __init__(self, pos, vel, mass, eps, offsets=None, precision="f64acc", G: float = 1.0,
-                 tune=None, device="cuda", stream=None, use_graph: bool = False):
+                 tune=None, device="cuda", stream=None, use_graph: bool = False,
+                 positions="default"):
         self.device = torch.device(device)
         self.pos = _dev_f64(pos, self.device)
         self.vel = _dev_f64(vel, self.device)
@@ -103,7 +104,8 @@ class System:
                                                                 precision=precision))
         self.acc = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
         self.pot = torch.zeros(n, dtype=torch.float64, device=self.device)
-        self.opts = B.make_opts(precision, G, stream, use_graph=use_graph, tune=tune)
+        self.opts = B.make_opts(precision, G, stream, use_graph=use_graph, tune=tune,
+                                positions=positions)
         if offsets is None:
             self.offsets = None
             self.eps_b = None

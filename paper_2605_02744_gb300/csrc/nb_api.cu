@@ -325,6 +325,8 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
     j.threads = o->tune ? o->tune->threads : 0;
+    j.positions = o->positions;
+    j.gamma = o->near_gamma;
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)ws;
@@ -351,6 +353,8 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
     j.threads = o->tune ? o->tune->threads : 0;
+    j.positions = o->positions;
+    j.gamma = o->near_gamma;
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)s->ws;

@@ -250,6 +250,8 @@ struct BatchedJob {
     int precision;
     int cluster;      // CTAs per thread-block cluster (0 = default)
     int threads;      // threads per CTA (0 = default)
+    int positions;    // nb_positions: SPLIT = hi/lo everywhere, else adaptive
+    float gamma;      // near/far threshold (0 = default)
     long long timeout;
     cudaStream_t stream;
     char *ws;

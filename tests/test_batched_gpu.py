@@ -58,11 +58,14 @@ def test_forces_batched_per_cluster(prec, cs, bt):
         assert rel_err(p[lo:hi], rp).max() <= TOL[prec], (c, SIZES[c])
 
 
-def test_step_batched_matches_oracle_per_cluster():
+@pytest.mark.parametrize("positions", ["default", "split"])
+def test_step_batched_matches_oracle_per_cluster(positions):
+    # 20 steps cross one Morton re-sort of every cluster (every 16 steps)
     sizes = [64, 65, 200, 1000, 3000, 7, 1, 8192]
     s = _batch(sizes, seed=3)
     eps = _eps(len(sizes), 1)
-    g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc")
+    g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc",
+                   positions=positions)
     g.step(1e-3, 20)
     assert g.poll() == binding.NB_OK
     x, v = host(g.pos), host(g.vel)
