@@ -3,14 +3,16 @@
 
 Metric: G pair-interactions/s on a 2^20-particle Plummer sphere (eps = 1e-3,
 FP32 pairs with Kahan-compensated accumulation), one step = one kick-drift-kick
-leapfrog step through nb_step (kick + drift + FP32 pack, the all-pairs
-force + potential kernel with the closing half-kick fused into its epilogue)
-followed by nb_energy.  Interactions are counted as N^2 per step (the self
-pair is evaluated).  Alongside: the FP64-accumulate variant's rate, the
-adjoint/forward time ratio of the 16384-particle, 200-step gradient, the
-roofline of the force kernel against the FP32 FMA peak (20 flops per
-interaction), the end-to-end rate from host buffers, and the FP64 oracle timed
-on the host cores on a sample of rows.
+leapfrog step through nb_step (kick + drift, Morton-sorted FP32 pack, the
+all-pairs force + potential evaluation, its fold with the closing half-kick)
+followed by nb_energy.  Interactions are counted as N^2 per step, the
+metric's convention; the default symmetric-pair path evaluates each
+unordered pair once and applies it to both particles (Newton's third law),
+the direct path (timed alongside) every ordered pair.  Alongside: the
+FP64-accumulate variant's rate, the adjoint/forward time ratio of the
+16384-particle, 200-step gradient, the roofline of the step against the FP32
+FMA peak (20 flops per interaction), the end-to-end rate from host buffers,
+and the FP64 oracle timed on the host cores on a sample of rows.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -39,7 +41,7 @@ EPS_MAIN = 1e-3
 DT_MAIN = 1e-4
 FLOPS_PER_INTERACTION = 20
 FP32_LANES_PER_SM = 128
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_sk_plummer_2p20_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_sym_plummer_2p20_traffic.txt")
 
 
 def _dist():
@@ -128,7 +130,7 @@ class ClockSampler:
 def _kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("nb_force.cu", "nb_device.cuh"):
+    for f in ("nb_sym.cu", "nb_device.cuh"):
         with open(os.path.join(ROOT, "paper_2605_02744_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -353,8 +355,11 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     results = {}
-    for prec in ("kahan", "f64acc"):
-        system = api.System(s.pos, s.vel, s.mass, EPS_MAIN, precision=prec, device=dev)
+    for prec, pairs in (("kahan", "default"), ("f64acc", "default"), ("kahan_direct", "direct")):
+        if prec == "kahan_direct" and args.skip_extra:
+            continue
+        system = api.System(s.pos, s.vel, s.mass, EPS_MAIN, precision=prec.split("_")[0],
+                            device=dev, pairs=pairs)
         system.forces()
         for _ in range(args.warmup):
             system.step(DT_MAIN, 1)
@@ -451,21 +456,24 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "Plummer sphere N=2^20 (1048576), equal mass, seed 0, eps=1e-3; "
-                               "one KDK step dt=1e-4 (FP32 pairs, Kahan accumulation, "
-                               "adaptive hi/lo displacement, FP64 state) + energy",
+                               "one KDK step dt=1e-4 (FP32 pairs, each unordered pair "
+                               "evaluated once, Kahan accumulation, adaptive hi/lo "
+                               "displacement, FP64 state) + energy",
                    "N": N_MAIN, "precision": "kahan", "interactions_per_step": "N^2",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "force_sk_kernel<512,2,1024,2,KAHAN,split,adaptive>",
+                     "kernel": "force_sym_kernel<KAHAN, adaptive> (+ sym_fold_kernel, "
+                               "sorted pack, kick-drift, energy inside the timed step)",
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{max_mhz:.0f} MHz (max SM clock)",
                      "frac_at_observed_clock": (achieved / (peak_tflops * obs / max_mhz)
                                                 if obs else None),
-                     "timing": "CUDA events around each nb_step+nb_energy (force kernel "
-                               "plus the O(N) and sort kernels) on the launching stream"},
+                     "timing": "CUDA events around each nb_step+nb_energy (pair kernel "
+                               "plus the fold, O(N) and sort kernels) on the launching "
+                               "stream"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
@@ -475,6 +483,8 @@ def run_ours(args):
         "variants": {"f64acc_value": ws * args.steps * inter / (sum(results["f64acc"][0]) * 1e-3)
                      / 1e9, "f64acc_ms_per_step": f64_ms,
                      "kahan_ms_per_step": step_ms,
+                     "kahan_direct_ms_per_step": (statistics.mean(results["kahan_direct"][0])
+                                                  if "kahan_direct" in results else None),
                      "lognormal_65536_per_precision": variants},
         "adjoint": adj,
         "batched": batched,
@@ -489,8 +499,9 @@ def run_ours(args):
 
 
 def run_profile_case(args):
-    """A few nb_forces calls at --profile N (Kahan, split positions): the
-    small and full-size cases the ncu captures under profiles/ were taken on."""
+    """A few nb_forces calls at --profile N (--precision, default positions
+    and pairs): the small and full-size cases of the ncu captures under
+    profiles/."""
     import torch
 
     import paper_2605_02744_gb300 as pkg

@@ -84,6 +84,23 @@ typedef enum {
                            their largest coordinate, SINGLE for the rest   */
 } nb_positions;
 
+/* How the pairs of one system (nb_forces, nb_step with B = 1) are evaluated
+ * by the FP32-pair policies.  DIRECT evaluates every ordered pair (i, j)
+ * once for particle i.  SYMMETRIC evaluates every unordered pair once and
+ * applies it to both particles: the pair term of Eq. 1 changes sign under
+ * i <-> j apart from the masses, so d, r^2 and r^-3 serve a_i and a_j
+ * (about 9 FP32 operations per directed interaction instead of 13).  It
+ * needs eps > 0 and a workspace of about N^2 / 256 bytes for the j-side
+ * partial sums (4.3 GB at N = 2^20), which nb_workspace_bytes includes when
+ * the path is in use.  DEFAULT takes SYMMETRIC for 32768 <= N <= 2^21 and
+ * eps > 0, DIRECT otherwise.  Results of both are deterministic; they
+ * differ from each other by summation order only. */
+typedef enum {
+    NB_PAIRS_DEFAULT = 0,
+    NB_PAIRS_DIRECT = 1,
+    NB_PAIRS_SYMMETRIC = 2
+} nb_pairs;
+
 /* Launch shape of the FP32-pair kernels.  Zero fields take the built-in
  * defaults for the problem size; nb_tune_valid() reports whether a shape
  * is one this build was compiled for. */
@@ -108,6 +125,7 @@ typedef struct nb_opts {
     float near_gamma;       /* NB_POS_ADAPTIVE: a tile pair is well separated
                                when its box gap >= near_gamma x the largest
                                coordinate magnitude; 0 = default (1/64)     */
+    int32_t pairs;          /* nb_pairs                                       */
 } nb_opts;
 
 /* Fills *opts with precision F64ACC, G = 1, default stream, no graph,

@@ -24,16 +24,18 @@ def _resolve_tune(tune, kind, precision, n, autotune):
 
 
 def forces(pos, mass, eps: float, precision="f64acc", G: float = 1.0, with_pot: bool = True,
-           tune=None, ws=None, stream=None):
+           tune=None, ws=None, stream=None, positions="default", pairs="default"):
     """(acc, pot) for one system; pos [N,3], mass [N] CUDA float64 tensors.
 
     tune: None (built-in shapes), an nb_tune dict, or "auto" (autotuner cache).
+    positions / pairs: nb_positions / nb_pairs names ("default", "split",
+    "single", "adaptive" / "default", "direct", "symmetric").
     """
     if tune == "auto":
         from . import tune as T
         tune = _resolve_tune(tune, "force", precision, mass.shape[0],
                              lambda: T.autotune_forces(pos, mass, eps, precision))
-    opts = B.make_opts(precision, G, stream, tune=tune)
+    opts = B.make_opts(precision, G, stream, tune=tune, positions=positions, pairs=pairs)
     n = mass.shape[0]
     acc = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
     pot = torch.empty(n, dtype=torch.float64, device=pos.device) if with_pot else None
@@ -85,7 +87,7 @@ class System:
 
     def __init__(self, pos, vel, mass, eps, offsets=None, precision="f64acc", G: float = 1.0,
                  tune=None, device="cuda", stream=None, use_graph: bool = False,
-                 positions="default"):
+                 positions="default", pairs="default"):
         self.device = torch.device(device)
         self.pos = _dev_f64(pos, self.device)
         self.vel = _dev_f64(vel, self.device)
@@ -105,7 +107,7 @@ class System:
         self.acc = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
         self.pot = torch.zeros(n, dtype=torch.float64, device=self.device)
         self.opts = B.make_opts(precision, G, stream, use_graph=use_graph, tune=tune,
-                                positions=positions)
+                                positions=positions, pairs=pairs)
         if offsets is None:
             self.offsets = None
             self.eps_b = None

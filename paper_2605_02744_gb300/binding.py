@@ -35,6 +35,11 @@ NB_POS_SINGLE = 2
 NB_POS_ADAPTIVE = 3
 POSITIONS = {"default": NB_POS_DEFAULT, "split": NB_POS_SPLIT, "single": NB_POS_SINGLE,
              "adaptive": NB_POS_ADAPTIVE}
+NB_PAIRS_DEFAULT = 0
+NB_PAIRS_DIRECT = 1
+NB_PAIRS_SYMMETRIC = 2
+PAIRS = {"default": NB_PAIRS_DEFAULT, "direct": NB_PAIRS_DIRECT,
+         "symmetric": NB_PAIRS_SYMMETRIC}
 
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
@@ -62,7 +67,8 @@ class nb_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("G", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32),
                 ("tune", ctypes.POINTER(nb_tune)), ("timeout_cycles", ctypes.c_int64),
-                ("positions", ctypes.c_int32), ("near_gamma", ctypes.c_float)]
+                ("positions", ctypes.c_int32), ("near_gamma", ctypes.c_float),
+                ("pairs", ctypes.c_int32)]
 
 
 class nb_state(ctypes.Structure):
@@ -145,7 +151,7 @@ def _dptr(t, name, dtype=None, optional=False):
 
 def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool = False,
               tune=None, timeout_cycles: int = 0, positions="default",
-              near_gamma: float = 0.0) -> nb_opts:
+              near_gamma: float = 0.0, pairs="default") -> nb_opts:
     """nb_opts for a call; stream None = torch's current stream on the current device."""
     o = nb_opts()
     lib().nb_opts_default(ctypes.byref(o))
@@ -164,6 +170,7 @@ def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool =
     o.timeout_cycles = int(timeout_cycles)
     o.positions = POSITIONS[positions] if isinstance(positions, str) else int(positions)
     o.near_gamma = float(near_gamma)
+    o.pairs = PAIRS[pairs] if isinstance(pairs, str) else int(pairs)
     return o
 
 

@@ -124,8 +124,23 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     off = align256(off + 2 * (size_t)L.max_grid * (size_t)L.record_bytes_per_i);
     L.scratch = off;
     off = align256(off + kScratchBase + batched_scratch_bytes(B));
+    if (sym_wanted(opts, N, B)) {
+        const SymSizes z = sym_sizes(L.Np);
+        L.sym_p = off;
+        L.sym_p_bytes = z.p_bytes;
+        off = align256(off + z.p_bytes);
+        L.sym_rec = off;
+        L.sym_rec_bytes = z.rec_bytes;
+        off = align256(off + z.rec_bytes);
+    }
     L.total = off;
     return L;
+}
+
+bool sym_wanted(const nb_opts *o, int64_t N, int32_t B) {
+    if (!o || B != 1 || o->precision == NB_PREC_FP64) return false;
+    if (o->pairs == NB_PAIRS_SYMMETRIC) return true;
+    return o->pairs == NB_PAIRS_DEFAULT && N >= kSymMinN && N <= kSymMaxN;
 }
 
 int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L) {
@@ -176,6 +191,8 @@ static int check_common(const nb_opts *o, int64_t N, double eps) {
     if (o->timeout_cycles < 0) return fail(NB_ERR_INVALID, "timeout_cycles must be >= 0");
     if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_ADAPTIVE)
         return fail(NB_ERR_INVALID, "unknown positions mode %d", o->positions);
+    if (o->pairs < NB_PAIRS_DEFAULT || o->pairs > NB_PAIRS_SYMMETRIC)
+        return fail(NB_ERR_INVALID, "unknown pairs mode %d", o->pairs);
     if (!(o->near_gamma >= 0.f) || !isfinite(o->near_gamma))
         return fail(NB_ERR_INVALID, "near_gamma must be finite and >= 0");
     return NB_OK;
@@ -218,6 +235,9 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     j->reuse_order = false;
     j->gamma = o->near_gamma > 0.f ? o->near_gamma : kNearFarGamma;
     j->packed_ready = false;
+    // the default takes the symmetric path only where it applies (eps > 0);
+    // an explicit NB_PAIRS_SYMMETRIC with eps = 0 is refused by the launcher
+    j->sym = sym_wanted(o, N, 1) && (eps > 0.0 || o->pairs == NB_PAIRS_SYMMETRIC);
     j->timeout = timeout_of(o);
     j->stream = (cudaStream_t)o->stream;
     j->ws = (char *)ws;
@@ -440,6 +460,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
         key.o.timeout_cycles = o->timeout_cycles;
         key.o.positions = o->positions;
         key.o.near_gamma = o->near_gamma;
+        key.o.pairs = o->pairs;
         if (o->tune) {
             key.t.threads = o->tune->threads;
             key.t.i_per_thread = o->tune->i_per_thread;

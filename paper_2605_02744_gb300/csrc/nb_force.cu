@@ -488,16 +488,22 @@ int launch_force(const ForceJob &j) {
     const Shape &sh0 = j.shape;
     const bool adaptive = j.adaptive && !guard;
     char *sb = j.ws + j.L.sortbuf;
+    if (j.sym && guard) return fail(NB_ERR_UNSUPPORTED, "symmetric pairs need eps > 0");
     if (adaptive) {
+        // boxes per 64 j-slots and per warp of i-slots (direct kernel), or per
+        // 32-slot j-set and 128-slot warp i-set (symmetric kernel)
+        const int tile_unit = j.sym ? 32 : 64;
+        const int block_unit = j.sym ? 128 : 32 * sh0.ipt;
         int rc = launch_sorted_pack(j.pos, j.mass, j.N, j.L.Np, soa, sort_perm(sb, j.L),
                                     sort_keys(sb), sort_box6(sb, j.L), sort_tile_boxes(sb, j.L),
-                                    64, sort_block_boxes(sb, j.L), 32 * sh0.ipt, j.reuse_order,
-                                    j.stream);
+                                    tile_unit, sort_block_boxes(sb, j.L), block_unit,
+                                    j.reuse_order, j.stream);
         if (rc) return rc;
     } else if (!j.packed_ready) {
         int rc = launch_pack(j.pos, j.mass, j.N, j.L.Np, soa, j.stream);
         if (rc) return rc;
     }
+    if (j.sym) return launch_force_sym(j, adaptive);
     const Shape &sh = j.shape;
     ForceParams p;
     p.soa = soa;

@@ -65,6 +65,9 @@ struct WsLayout {
     size_t sortbuf;   // Morton keys, permutation, tile/block boxes (adaptive path)
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
+    size_t sym_p;     // symmetric-pair path: FP32 j-side partials per block pair
+    size_t sym_rec;   // symmetric-pair path: FP64 i-side records per row segment
+    size_t sym_p_bytes, sym_rec_bytes;  // 0 when the path is not provisioned
     size_t total;
     int64_t Np;       // padded particle count of the pack arrays
     int64_t max_blocks;
@@ -103,6 +106,7 @@ struct ForceJob {
     bool reuse_order;   // adaptive: keep the previous call's Morton order
     float gamma;        // near/far threshold of the adaptive path
     bool packed_ready;  // packA already holds float positions of `pos`
+    bool sym;           // symmetric-pair evaluation (nb_pairs resolved)
     long long timeout;
     cudaStream_t stream;
     char *ws;
@@ -138,13 +142,13 @@ inline float *sort_tile_boxes(char *sb, const WsLayout &L) {
     return reinterpret_cast<float *>(sb + 8 * sort_keys_len(L.Np) + 4 * L.Np);
 }
 inline float *sort_block_boxes(char *sb, const WsLayout &L) {
-    return sort_tile_boxes(sb, L) + 8 * (L.Np / 64 + 1);
+    return sort_tile_boxes(sb, L) + 8 * (L.Np / 32 + 1);
 }
 inline long long *sort_box6(char *sb, const WsLayout &L) {
     return reinterpret_cast<long long *>(sort_block_boxes(sb, L) + 8 * (L.Np / 32 + 1));
 }
 inline size_t sortbuf_bytes(int64_t Np) {
-    return 8 * (size_t)sort_keys_len(Np) + 4 * (size_t)Np + 32 * (size_t)(Np / 64 + 1) +
+    return 8 * (size_t)sort_keys_len(Np) + 4 * (size_t)Np + 32 * (size_t)(Np / 32 + 1) +
            32 * (size_t)(Np / 32 + 1) + 64;
 }
 // reuse_order: the keys already hold a Morton order of these N particles
@@ -173,6 +177,23 @@ __host__ __device__ inline void store_packed(float *soa, int64_t Np, int64_t i, 
 int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,
                 cudaStream_t st);
 int launch_force(const ForceJob &job);
+
+// ------------------------------------------------- symmetric-pair path
+// Row blocks of 2048 slots; items are the block pairs (I, J >= I).
+constexpr int64_t kSymBlock = 2048;
+// Default size range of the symmetric-pair path (the j-side partials take
+// nb (nb - 1) / 2 x 32 KiB, nb = N / 2048: 4.3 GB at N = 2^20).
+constexpr int64_t kSymMinN = 1 << 15;
+constexpr int64_t kSymMaxN = 1 << 21;
+struct SymSizes {
+    int64_t nb, T, U, ctas, K;  // row blocks, items, stream-K units, CTAs, records per row
+    size_t p_bytes, rec_bytes;
+};
+SymSizes sym_sizes(int64_t Np);
+// Whether the symmetric-pair path is provisioned / taken for N particles in
+// B clusters under opts (nb_pairs; FP32-pair policies, single systems).
+bool sym_wanted(const nb_opts *opts, int64_t N, int32_t B);
+int launch_force_sym(const ForceJob &job, bool adaptive);
 
 struct VjpJob {
     const double *pos;

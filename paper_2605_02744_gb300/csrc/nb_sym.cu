@@ -1,0 +1,487 @@
+// Symmetric-pair force evaluation (Eq. 1 with Newton's third law).
+//
+// The pair term of Eq. 1 is antisymmetric up to the masses: with
+// d = x_j - x_i and r^-3 = (|d|^2 + eps^2)^-3/2,
+//     a_i += m_j r^-3 d,   a_j -= m_i r^-3 d,
+//     phi_i += m_j r^-1,   phi_j += m_i r^-1,
+// so one evaluation of d, r^2, r^-1 and r^-3 serves both particles.  Per
+// unordered pair that is 18 FP32 operations (single-float displacement) in
+// place of 2 x 13, about 9 per directed interaction.
+//
+// Decomposition.  The (padded) slots are cut into row blocks of 2048; the
+// work items are the block pairs (I, J) with J >= I, in row-major order,
+// cut into units of 4 j-sets and split evenly over one persistent CTA per SM
+// (stream-K: a CTA's range may start or end inside an item).
+// A CTA keeps block I in registers: warp w holds the 128 slots
+// I*2048 + w*128 + [0, 128), lane l the four slots  + 32k + l  (k = 0..3,
+// two packed f32x2 pairs).  For every 32-slot j-set of block J each warp
+// loads one j-particle per lane and rotates the set through its lanes with
+// shuffles: at step s lane l holds j-slot (l + s) mod 32, so in 32 steps
+// every lane meets every j once, and the j-particle's own sums (a_j, phi_j)
+// travel with it and come home to lane l.
+//
+//   * Off-diagonal items (I < J): both halves of every pair.  The 16 warps'
+//     j-side sums of 4 j-sets are added in warp order in shared memory (one
+//     barrier per 4 j-sets) and stored as the FP32 partial P[I, J] of the
+//     J-block particles.
+//   * Diagonal items (I = J): the i-side only, over all ordered pairs of
+//     the block; the self pair (j-set 4w + k at rotation step 0 for lane
+//     slot k of warp w) gets a zero mass, so Eq. 1's j != i holds exactly.
+//
+// The i-side FP32 sums are folded into the accumulation policy (FP32,
+// Kahan or FP64; totals kept in shared memory) every 16 j-sets, and stored
+// once per row segment as an FP64 record.  A second kernel adds, slot by
+// slot in a fixed order, the records of the row's CTAs and the partials
+// P[I', I] for I' < I, applies G, scatters through the Morton permutation
+// and optionally kicks the velocity.  Every
+// sum runs in a fixed order: results are bitwise reproducible.
+//
+// Displacements: single floats, hi/lo pairs (x_j.hi - x_i.hi) +
+// (x_j.lo - x_i.lo), or adaptive: per (warp i-set, j-set) the hi/lo form
+// only when the bounding boxes are closer than gamma * max|x| (a 64-bit
+// mask per warp and item, from the Morton-sorted pack's boxes).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nb {
+
+using dev::Acc;
+using dev::add2;
+using dev::f2;
+using dev::fma2;
+using dev::mul2;
+using dev::rsqrt_approx;
+
+namespace {
+
+constexpr int NW = 16;              // warps per CTA
+constexpr int NT = NW * 32;         // threads per CTA
+constexpr int IR = 4;               // i-slots per lane (two packed pairs)
+constexpr int BI = NW * 32 * IR;    // slots per row block
+constexpr int JS = 32;              // slots per j-set (one per lane)
+constexpr int NJS = BI / JS;        // j-sets per block
+constexpr int KB = 4;               // j-sets per cross-warp reduction
+constexpr int FL = 16;              // j-sets per i-side policy flush
+constexpr int US = NJS / KB;        // stream-K units (KB j-sets) per item
+static_assert(BI == kSymBlock, "row block size");
+static_assert(KB * JS * 4 == NT, "one reduced value per thread");
+static_assert(NJS % KB == 0 && NJS % FL == 0, "groups tile a block");
+constexpr size_t kRedBytes = 2 * KB * NW * 32 * sizeof(float4);
+
+struct SymParams {
+    const float *soa;   // packed SoA [7][Np]
+    int64_t Np;
+    int64_t nb;         // row blocks
+    int64_t T;          // items nb (nb + 1) / 2
+    int64_t U;          // stream-K units T * US (KB j-sets of one item each)
+    int64_t ctas;       // grid size of the pair kernel
+    int64_t K;          // record slots per row
+    float eps2;
+    float gamma;        // adaptive threshold; the mode decides whether it is used
+    const float *jbox;  // per 32 slots: lo[3], hi[3], max|x|, pad
+    const float *wbox;  // per 128 slots
+    float *P;           // [nb (nb - 1) / 2][BI][4]
+    double *rec;        // [nb][K][BI][4]
+};
+
+__host__ __device__ inline int64_t row_start(int64_t I, int64_t nb) {
+    return I * nb - I * (I - 1) / 2;
+}
+
+__device__ __forceinline__ bool boxes_near(const float *a, const float *b, float gamma) {
+    float g2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gap = fmaxf(0.f, fmaxf(b[c] - a[3 + c], a[c] - b[3 + c]));
+        g2 = fmaf(gap, gap, g2);
+    }
+    const float X = gamma * fmaxf(a[6], b[6]);
+    return g2 < X * X;
+}
+
+// i-side state of one lane: four slots as two packed pairs (g = 0, 1).
+struct ISet {
+    float2 nx[2], ny[2], nz[2];     // -x.hi
+    float2 nxl[2], nyl[2], nzl[2];  // -x.lo
+    float2 m[2], nm[2];             // m_i, -m_i
+    float2 ax[2], ay[2], az[2], ph[2];
+};
+
+// One rotation step: the lane's four i-slots against its current j.  With
+// SELF, i-slot self_k is the j-particle itself: its half of the pair gets a
+// zero mass (Eq. 1 leaves out j = i).
+template <bool NEAR, bool SYM, bool SELF>
+__device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float jy, float jz,
+                                     float jm, float jxl, float jyl, float jzl, float &bx,
+                                     float &by, float &bz, float &bp, int self_k = -1) {
+    const float2 X = f2(jx, jx), Y = f2(jy, jy), Z = f2(jz, jz);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const float2 M = SELF ? f2(self_k == 2 * g ? 0.f : jm, self_k == 2 * g + 1 ? 0.f : jm)
+                              : f2(jm, jm);
+        float2 dx = add2(X, S.nx[g]);
+        float2 dy = add2(Y, S.ny[g]);
+        float2 dz = add2(Z, S.nz[g]);
+        if (NEAR) {
+            dx = add2(dx, add2(f2(jxl, jxl), S.nxl[g]));
+            dy = add2(dy, add2(f2(jyl, jyl), S.nyl[g]));
+            dz = add2(dz, add2(f2(jzl, jzl), S.nzl[g]));
+        }
+        float2 r2 = fma2(dx, dx, e2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        const float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 ri3 = mul2(mul2(ri, ri), ri);
+        const float2 sj = mul2(M, ri3);
+        S.ax[g] = fma2(sj, dx, S.ax[g]);
+        S.ay[g] = fma2(sj, dy, S.ay[g]);
+        S.az[g] = fma2(sj, dz, S.az[g]);
+        S.ph[g] = fma2(M, ri, S.ph[g]);
+        if (SYM) {
+            const float2 si = mul2(S.nm[g], ri3);  // -m_i r^-3
+            bx = fmaf(si.x, dx.x, bx);
+            bx = fmaf(si.y, dx.y, bx);
+            by = fmaf(si.x, dy.x, by);
+            by = fmaf(si.y, dy.y, by);
+            bz = fmaf(si.x, dz.x, bz);
+            bz = fmaf(si.y, dz.y, bz);
+            bp = fmaf(S.m[g].x, ri.x, bp);
+            bp = fmaf(S.m[g].y, ri.y, bp);
+        }
+    }
+}
+
+// 32 steps over one j-set; the j values (and sums) end on their home lane.
+// self_k >= 0 (diagonal items only): the j-set is the warp's own i-slots
+// 32 self_k + [0, 32), so step 0 pairs every lane with itself.
+template <bool NEAR, bool SYM>
+__device__ __forceinline__ void rotate_set(ISet &S, const float2 e2, const float (&j)[7],
+                                           float4 &b, int self_k) {
+    const int src = (threadIdx.x + 1) & 31;
+    float jx = j[0], jy = j[1], jz = j[2], jm = j[3], jxl = j[4], jyl = j[5], jzl = j[6];
+    float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+    auto rotate = [&]() {
+        jx = __shfl_sync(0xffffffffu, jx, src);
+        jy = __shfl_sync(0xffffffffu, jy, src);
+        jz = __shfl_sync(0xffffffffu, jz, src);
+        jm = __shfl_sync(0xffffffffu, jm, src);
+        if (NEAR) {
+            jxl = __shfl_sync(0xffffffffu, jxl, src);
+            jyl = __shfl_sync(0xffffffffu, jyl, src);
+            jzl = __shfl_sync(0xffffffffu, jzl, src);
+        }
+        if (SYM) {
+            bx = __shfl_sync(0xffffffffu, bx, src);
+            by = __shfl_sync(0xffffffffu, by, src);
+            bz = __shfl_sync(0xffffffffu, bz, src);
+            bp = __shfl_sync(0xffffffffu, bp, src);
+        }
+    };
+    int s0 = 0;
+    if (self_k >= 0) {
+        step<NEAR, SYM, true>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp, self_k);
+        rotate();
+        s0 = 1;
+    }
+#pragma unroll 4
+    for (int s = s0; s < JS; ++s) {
+        step<NEAR, SYM, false>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp);
+        rotate();
+    }
+    b = make_float4(bx, by, bz, bp);
+}
+
+template <int MODE, bool SYM>
+__device__ __forceinline__ void run_set(ISet &S, const float2 e2, const float (&j)[7], bool near,
+                                        float4 &b, int self_k) {
+    if (MODE == 1 || (MODE == 2 && near))
+        rotate_set<true, SYM>(S, e2, j, b, self_k);
+    else
+        rotate_set<false, SYM>(S, e2, j, b, self_k);
+}
+
+__device__ __forceinline__ void load_j(const SymParams &p, int64_t s, float (&j)[7]) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a) j[a] = __ldg(p.soa + a * p.Np + s);
+}
+
+// MODE: 0 single-float displacement, 1 hi/lo, 2 adaptive.
+template <int POL, int MODE>
+__global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *red = reinterpret_cast<float4 *>(smem);                   // [2][KB][NW][32]
+    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smem + kRedBytes);   // [16][NT]
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    const int64_t c = blockIdx.x;
+    int64_t u = sk_lo(p.U, p.ctas, c);
+    const int64_t u_end = sk_lo(p.U, p.ctas, c + 1);
+    if (u >= u_end) return;
+    const int64_t t0 = u / US;
+    int64_t I = 0;
+    while (row_start(I + 1, p.nb) <= t0) ++I;
+    int64_t J = I + (t0 - row_start(I, p.nb));
+    const float2 e2 = f2(p.eps2, p.eps2);
+    ISet S;
+    int half = 0;
+    bool row_open = false;
+    while (u < u_end) {
+        // this CTA's j-sets [qa, qb) of item (I, J)
+        const int qa = (int)(u % US) * KB;
+        const int64_t item_end = (u / US + 1) * US;
+        const int64_t seg_end = item_end < u_end ? item_end : u_end;
+        const int qb = qa + (int)(seg_end - u) * KB;
+        const int64_t ib = I * BI + w * 128;  // this warp's i-set
+        if (!row_open) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                float v[2][7];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) load_j(p, ib + 32 * (2 * g + h) + l, v[h]);
+                S.nx[g] = f2(-v[0][0], -v[1][0]);
+                S.ny[g] = f2(-v[0][1], -v[1][1]);
+                S.nz[g] = f2(-v[0][2], -v[1][2]);
+                S.m[g] = f2(v[0][3], v[1][3]);
+                S.nm[g] = f2(-v[0][3], -v[1][3]);
+                S.nxl[g] = f2(-v[0][4], -v[1][4]);
+                S.nyl[g] = f2(-v[0][5], -v[1][5]);
+                S.nzl[g] = f2(-v[0][6], -v[1][6]);
+                S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 16; ++v) tot[v * NT + tid].zero();
+            row_open = true;
+        }
+        const bool sym = J != I;
+        const int64_t jb = J * BI;
+        // near mask of this warp's i-set against the block's 64 j-sets
+        unsigned long long near = 0ull;
+        if (MODE == 2) {
+            float wb[7];
+#pragma unroll
+            for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + (ib / 128) * 8 + a);
+            float tb[2][7];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int a = 0; a < 7; ++a) tb[h][a] = __ldg(p.jbox + (jb / JS + l + 32 * h) * 8 + a);
+            const unsigned lo = __ballot_sync(0xffffffffu, boxes_near(wb, tb[0], p.gamma));
+            const unsigned hi = __ballot_sync(0xffffffffu, boxes_near(wb, tb[1], p.gamma));
+            near = ((unsigned long long)hi << 32) | lo;
+        }
+        const int64_t pidx = J * (J - 1) / 2 + I;
+        float jn[7];
+        load_j(p, jb + qa * JS + l, jn);
+        for (int q = qa; q < qb; ++q) {
+            float jc[7];
+#pragma unroll
+            for (int a = 0; a < 7; ++a) jc[a] = jn[a];
+            if (q + 1 < qb) load_j(p, jb + (q + 1) * JS + l, jn);
+            const bool nq = (near >> q) & 1ull;
+            float4 b;
+            if (sym) {
+                run_set<MODE, true>(S, e2, jc, nq, b, -1);
+                red[((half * KB + (q % KB)) * NW + w) * 32 + l] = b;
+            } else {
+                run_set<MODE, false>(S, e2, jc, nq, b, (q >> 2) == w ? (q & 3) : -1);
+            }
+            if ((q + 1) % FL == 0 || q + 1 == qb) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const float2 v4[4] = {S.ax[g], S.ay[g], S.az[g], S.ph[g]};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        tot[((2 * g) * 4 + e) * NT + tid].add(v4[e].x);
+                        tot[((2 * g + 1) * 4 + e) * NT + tid].add(v4[e].y);
+                    }
+                    S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+                }
+            }
+            if (sym && (q + 1) % KB == 0) {
+                __syncthreads();
+                const int qq = tid >> 7, ll = (tid >> 2) & 31, e = tid & 3;
+                const float *r =
+                    reinterpret_cast<const float *>(red) + ((half * KB + qq) * NW * 32 + ll) * 4 + e;
+                float s = 0.f;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; ++w2) s += r[w2 * 32 * 4];
+                p.P[((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e] = s;
+                half ^= 1;
+            }
+        }
+        u = seg_end;
+        if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
+            // row segment done: FP64 record of the policy totals
+            const int64_t k = c - sk_owner(p.U, p.ctas, row_start(I, p.nb) * US);
+#pragma unroll
+            for (int kk = 0; kk < IR; ++kk) {
+                const int64_t slot = w * 128 + 32 * kk + l;
+                double *r = p.rec + (((I * p.K + k) * BI) + slot) * 4;
+                reinterpret_cast<double2 *>(r)[0] =
+                    make_double2(tot[(kk * 4 + 0) * NT + tid].value(), tot[(kk * 4 + 1) * NT + tid].value());
+                reinterpret_cast<double2 *>(r)[1] =
+                    make_double2(tot[(kk * 4 + 2) * NT + tid].value(), tot[(kk * 4 + 3) * NT + tid].value());
+            }
+            row_open = false;
+        }
+        if (qb == NJS && ++J == p.nb) {
+            ++I;
+            J = I;
+        }
+    }
+}
+
+// Adds an FP64 record value in the policy's arithmetic.
+template <int POL>
+__device__ __forceinline__ void add_record(Acc<POL> &a, double v);
+template <>
+__device__ __forceinline__ void add_record<NB_PREC_FP32>(Acc<NB_PREC_FP32> &a, double v) {
+    a.add((float)v);
+}
+template <>
+__device__ __forceinline__ void add_record<NB_PREC_KAHAN>(Acc<NB_PREC_KAHAN> &a, double v) {
+    const float h = (float)v;
+    a.add(h);
+    a.add((float)(v - (double)h));
+}
+template <>
+__device__ __forceinline__ void add_record<NB_PREC_F64ACC>(Acc<NB_PREC_F64ACC> &a, double v) {
+    a.s += v;
+}
+
+template <int POL>
+__global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_t N,
+                                                       const int *__restrict__ perm, double G,
+                                                       double *__restrict__ acc,
+                                                       double *__restrict__ pot,
+                                                       double *__restrict__ vel, double kick,
+                                                       uint32_t *status) {
+    uint32_t bad = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = s / BI, r = s % BI;
+        Acc<POL> a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a[e].zero();
+        const int64_t rs = row_start(I, p.nb);
+        const int64_t c0 = sk_owner(p.U, p.ctas, rs * US);
+        const int64_t c1 = sk_owner(p.U, p.ctas, (rs + (p.nb - I)) * US - 1);
+        for (int64_t k = 0; k <= c1 - c0; ++k) {
+            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + (((I * p.K + k) * BI) + r) * 4);
+            const double2 u = __ldg(rr), v = __ldg(rr + 1);
+            add_record<POL>(a[0], u.x);
+            add_record<POL>(a[1], u.y);
+            add_record<POL>(a[2], v.x);
+            add_record<POL>(a[3], v.y);
+        }
+        const float4 *P4 = reinterpret_cast<const float4 *>(p.P) + (I * (I - 1) / 2) * BI + r;
+        for (int64_t i2 = 0; i2 < I; ++i2) {
+            const float4 v = __ldcs(P4 + i2 * BI);
+            a[0].add(v.x);
+            a[1].add(v.y);
+            a[2].add(v.z);
+            a[3].add(v.w);
+        }
+        const double ph = a[3].value();
+        const double ax = G * a[0].value(), ay = G * a[1].value(), az = G * a[2].value();
+        const double gp = -G * ph;
+        const int64_t i = perm ? (int64_t)perm[s] : s;
+        acc[3 * i] = ax;
+        acc[3 * i + 1] = ay;
+        acc[3 * i + 2] = az;
+        if (vel) {
+            vel[3 * i] += kick * ax;
+            vel[3 * i + 1] += kick * ay;
+            vel[3 * i + 2] += kick * az;
+        }
+        if (pot) pot[i] = gp;
+        if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
+    }
+    if (bad) dev::set_status(status, kStatusNonFinite);
+}
+
+template <int POL, int MODE>
+int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint32_t *status) {
+    auto kern = force_sym_kernel<POL, MODE>;
+    const size_t smem = kRedBytes + 16 * NT * sizeof(Acc<POL>);
+    static const cudaError_t optin =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NB_CUDA(optin);
+    kern<<<(unsigned)p.ctas, NT, smem, j.stream>>>(p);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
+    sym_fold_kernel<POL><<<(unsigned)fold_blocks, 256, 0, j.stream>>>(
+        p, j.N, perm, j.G, j.acc, j.pot, j.vel, j.kick, status);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <int POL>
+int launch_sym_pol(const SymParams &p, const ForceJob &j, int mode, const int *perm,
+                   uint32_t *status) {
+    switch (mode) {
+        case 0: return launch_sym_mode<POL, 0>(p, j, perm, status);
+        case 1: return launch_sym_mode<POL, 1>(p, j, perm, status);
+        default: return launch_sym_mode<POL, 2>(p, j, perm, status);
+    }
+}
+
+}  // namespace
+
+SymSizes sym_sizes(int64_t Np) {
+    SymSizes z{};
+    z.nb = cdiv(Np, kSymBlock);
+    z.T = z.nb * (z.nb + 1) / 2;
+    z.U = z.T * US;
+    z.ctas = std::min<int64_t>(device_sm_count(), z.U);
+    int64_t K = 1;
+    for (int64_t I = 0; I < z.nb; ++I) {
+        const int64_t rs = row_start(I, z.nb);
+        const int64_t k = sk_owner(z.U, z.ctas, (rs + (z.nb - I)) * US - 1) -
+                          sk_owner(z.U, z.ctas, rs * US) + 1;
+        K = std::max(K, k);
+    }
+    z.K = K;
+    z.p_bytes = (size_t)(z.nb * (z.nb - 1) / 2) * kSymBlock * 16;
+    z.rec_bytes = (size_t)z.nb * (size_t)K * kSymBlock * 32;
+    return z;
+}
+
+int launch_force_sym(const ForceJob &j, bool adaptive) {
+    if (j.eps <= 0.0) return fail(NB_ERR_UNSUPPORTED, "symmetric pairs need eps > 0");
+    if (j.L.sym_rec_bytes == 0)
+        return fail(NB_ERR_WORKSPACE, "workspace has no symmetric-pair buffers");
+    const SymSizes z = sym_sizes(j.L.Np);
+    SymParams p;
+    char *sb = j.ws + j.L.sortbuf;
+    p.soa = reinterpret_cast<const float *>(j.ws + j.L.packA);
+    p.Np = j.L.Np;
+    p.nb = z.nb;
+    p.T = z.T;
+    p.U = z.U;
+    p.ctas = z.ctas;
+    p.K = z.K;
+    const float ef = (float)j.eps;
+    p.eps2 = ef * ef;
+    p.gamma = j.gamma;
+    p.jbox = adaptive ? sort_tile_boxes(sb, j.L) : nullptr;
+    p.wbox = adaptive ? sort_block_boxes(sb, j.L) : nullptr;
+    p.P = reinterpret_cast<float *>(j.ws + j.L.sym_p);
+    p.rec = reinterpret_cast<double *>(j.ws + j.L.sym_rec);
+    const int *perm = adaptive ? sort_perm(sb, j.L) : nullptr;
+    uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
+    const int mode = adaptive ? 2 : (j.split ? 1 : 0);
+    switch (j.precision) {
+        case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, mode, perm, status);
+        case NB_PREC_KAHAN: return launch_sym_pol<NB_PREC_KAHAN>(p, j, mode, perm, status);
+        case NB_PREC_F64ACC: return launch_sym_pol<NB_PREC_F64ACC>(p, j, mode, perm, status);
+    }
+    return fail(NB_ERR_UNSUPPORTED, "symmetric pairs compute FP32 pairs (FP32, KAHAN, F64ACC)");
+}
+
+}  // namespace nb

@@ -101,7 +101,11 @@ def _cost(t: dict) -> tuple:
 
 def autotune_forces(pos, mass, eps: float, precision="kahan", reps: int = 5, warmup: int = 2,
                     candidates=None, store: bool = True) -> dict:
-    """Time nb_forces for every compiled candidate; returns the best nb_tune dict."""
+    """Time nb_forces for every compiled candidate; returns the best nb_tune dict.
+
+    The candidates are shapes of the direct (every ordered pair) kernel, which
+    is what is timed; the symmetric-pair path has one fixed shape.
+    """
     n = mass.shape[0]
     acc = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
     pot = torch.empty(n, dtype=torch.float64, device=pos.device)
@@ -109,7 +113,7 @@ def autotune_forces(pos, mass, eps: float, precision="kahan", reps: int = 5, war
     for cand in candidates or FORCE_CANDIDATES:
         if not B.nb_tune_valid(cand):
             continue
-        opts = B.make_opts(precision, tune=cand)
+        opts = B.make_opts(precision, tune=cand, pairs="direct")
         ws = B.workspace(n, 1, opts, pos.device)
         run = lambda: B.nb_forces(pos, mass, eps, acc, pot, ws, opts)
         for _ in range(warmup):

@@ -139,3 +139,26 @@ def test_python_binding_requires_cuda_tensors(B):
     x = torch.zeros((4, 3), dtype=torch.float64)
     with pytest.raises(TypeError):
         B.nb_forces(x, x[:, 0].contiguous(), 0.1, x, None, torch.zeros(256, dtype=torch.uint8), o)
+
+
+def test_pairs_option_and_symmetric_workspace(B):
+    o = _opts(B)
+    assert o.pairs == B.NB_PAIRS_DEFAULT
+    n = 1 << 20
+    nb = n // 2048
+    partials = nb * (nb - 1) // 2 * 2048 * 16  # FP32 (a, phi) per j-block slot and block pair
+    default = B.nb_workspace_bytes(n, 1, o)
+    direct = B.nb_workspace_bytes(n, 1, _opts(B, pairs=B.NB_PAIRS_DIRECT))
+    assert default - direct >= partials
+    # below the default range only an explicit request provisions the path
+    small_default = B.nb_workspace_bytes(1000, 1, o)
+    small_sym = B.nb_workspace_bytes(1000, 1, _opts(B, pairs=B.NB_PAIRS_SYMMETRIC))
+    assert small_sym > small_default
+    # FP64 pairs and batched systems never take it
+    assert B.nb_workspace_bytes(n, 1, _opts(B, precision=B.NB_PREC_FP64)) < default
+    assert B.nb_workspace_bytes(n, 4, o) < default
+
+
+def test_unknown_pairs_mode_is_rejected(B):
+    rc = _forces(B, opts=_opts(B, pairs=7))
+    assert rc == B.NB_ERR_INVALID

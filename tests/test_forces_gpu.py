@@ -123,9 +123,11 @@ def test_lognormal_65536_three_variants():
             assert ea <= TOL[prec] and ep <= TOL[prec], (prec, ea, ep)
 
 
+@pytest.mark.parametrize("pairs", ["default", "direct"])
 @pytest.mark.parametrize("prec", ["kahan", "f64acc"])
-def test_plummer_2pow20_sampled_rows(prec):
-    # the 2^20-particle evaluation in the benchmark's launch shape; exact
+def test_plummer_2pow20_sampled_rows(prec, pairs):
+    # the 2^20-particle evaluation in the benchmark's launch shape (the
+    # default is the symmetric-pair path) and in the direct kernel; exact
     # oracle rows for 1024 random particles plus the 64 innermost/outermost
     n = 1 << 20
     s = ics.plummer(n, seed=0)
@@ -133,7 +135,7 @@ def test_plummer_2pow20_sampled_rows(prec):
     order = np.argsort(r)
     rows = np.unique(np.concatenate([np.random.default_rng(4).choice(n, 1024, replace=False),
                                      order[:64], order[-64:]]))
-    a, p = api.forces(dev(s.pos), dev(s.mass), 1e-3, precision=prec)
+    a, p = api.forces(dev(s.pos), dev(s.mass), 1e-3, precision=prec, pairs=pairs)
     ra, rp = oracle.forces_rows(s.pos, s.mass, 1e-3, rows)
     ea = rel_vec_err(host(a)[rows], ra)
     ep = rel_err(host(p)[rows], rp)
