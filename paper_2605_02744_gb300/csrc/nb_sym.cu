@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
                 float s = 0.f;
 #pragma unroll
                 for (int w2 = 0; w2 < NW; ++w2) s += r[w2 * 32 * 4];
-                p.P[((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e] = s;
+                // streaming store: the partials are read once, by the fold, and must
+                // not evict the packed positions that every CTA re-reads from L2
+                __stcs(p.P + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, s);
                 half ^= 1;
             }
         }
@@ -347,10 +349,12 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
             for (int kk = 0; kk < IR; ++kk) {
                 const int64_t slot = w * 128 + 32 * kk + l;
                 double *r = p.rec + (((I * p.K + k) * BI) + slot) * 4;
-                reinterpret_cast<double2 *>(r)[0] =
-                    make_double2(tot[(kk * 4 + 0) * NT + tid].value(), tot[(kk * 4 + 1) * NT + tid].value());
-                reinterpret_cast<double2 *>(r)[1] =
-                    make_double2(tot[(kk * 4 + 2) * NT + tid].value(), tot[(kk * 4 + 3) * NT + tid].value());
+                __stcs(reinterpret_cast<double2 *>(r),
+                       make_double2(tot[(kk * 4 + 0) * NT + tid].value(),
+                                    tot[(kk * 4 + 1) * NT + tid].value()));
+                __stcs(reinterpret_cast<double2 *>(r) + 1,
+                       make_double2(tot[(kk * 4 + 2) * NT + tid].value(),
+                                    tot[(kk * 4 + 3) * NT + tid].value()));
             }
             row_open = false;
         }
