@@ -132,6 +132,8 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
         L.sym_rec = off;
         L.sym_rec_bytes = z.rec_bytes;
         off = align256(off + z.rec_bytes);
+        L.sym_cost = off;
+        off = align256(off + z.cost_bytes);
     }
     L.total = off;
     return L;

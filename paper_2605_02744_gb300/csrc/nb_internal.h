@@ -67,6 +67,7 @@ struct WsLayout {
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
     size_t sym_p;     // symmetric-pair path: FP32 j-side partials per block pair
     size_t sym_rec;   // symmetric-pair path: FP64 i-side records per row segment
+    size_t sym_cost;  // symmetric-pair path: item costs, their prefix, CTA ranges
     size_t sym_p_bytes, sym_rec_bytes;  // 0 when the path is not provisioned
     size_t total;
     int64_t Np;       // padded particle count of the pack arrays
@@ -79,6 +80,7 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts);
 int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Stream-K split: CTA c of C owns linear work items [lo(c), lo(c+1)) of T.
@@ -187,7 +189,7 @@ constexpr int64_t kSymMinN = 1 << 15;
 constexpr int64_t kSymMaxN = 1 << 21;
 struct SymSizes {
     int64_t nb, T, U, ctas, K;  // row blocks, items, stream-K units, CTAs, records per row
-    size_t p_bytes, rec_bytes;
+    size_t p_bytes, rec_bytes, cost_bytes;
 };
 SymSizes sym_sizes(int64_t Np);
 // Whether the symmetric-pair path is provisioned / taken for N particles in

@@ -10,8 +10,11 @@
 //
 // Decomposition.  The (padded) slots are cut into row blocks of 2048; the
 // work items are the block pairs (I, J) with J >= I, in row-major order,
-// cut into units of 4 j-sets and split evenly over one persistent CTA per SM
-// (stream-K: a CTA's range may start or end inside an item).
+// cut into units of 4 j-sets and split over one persistent CTA per SM into
+// contiguous ranges of equal estimated cost (stream-K: a range may start or
+// end inside an item).  The estimate counts FP32 operations per (warp,
+// j-set) from the same near/far box tests the pair kernel makes; three small
+// kernels compute it, scan it and cut the ranges.
 // A CTA keeps block I in registers: warp w holds the 128 slots
 // I*2048 + w*128 + [0, 128), lane l the four slots  + 32k + l  (k = 0..3,
 // two packed f32x2 pairs).  For every 32-slot j-set of block J each warp
@@ -50,6 +53,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "nb_device.cuh"
 #include "nb_internal.h"
@@ -94,10 +98,26 @@ struct SymParams {
     const float *wbox;  // per 128 slots
     float *P;           // [nb (nb - 1) / 2][BI][4]
     double *rec;        // [nb][K][BI][4]
+    const int64_t *lo;  // [ctas + 1]: CTA c owns units [lo[c], lo[c + 1])
+    uint32_t *status;
 };
 
 __host__ __device__ inline int64_t row_start(int64_t I, int64_t nb) {
     return I * nb - I * (I - 1) / 2;
+}
+
+// The CTA whose unit range holds unit u: the last c with lo[c] <= u (the
+// ranges are contiguous and ordered; empty ranges are never the answer).
+__device__ __forceinline__ int64_t range_owner(const int64_t *lo, int64_t ctas, int64_t u) {
+    int64_t a = 0, b = ctas - 1;
+    while (a < b) {
+        const int64_t m = (a + b + 1) / 2;
+        if (__ldg(lo + m) <= u)
+            a = m;
+        else
+            b = m - 1;
+    }
+    return a;
 }
 
 __device__ __forceinline__ bool boxes_near(const float *a, const float *b, float gamma) {
@@ -227,8 +247,8 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
     float *mid = reinterpret_cast<float *>(smem + kRedBytes + 16 * NT * sizeof(Acc<POL>));
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     const int64_t c = blockIdx.x;
-    int64_t u = sk_lo(p.U, p.ctas, c);
-    const int64_t u_end = sk_lo(p.U, p.ctas, c + 1);
+    int64_t u = __ldg(p.lo + c);
+    const int64_t u_end = __ldg(p.lo + c + 1);
     if (u >= u_end) return;
     const int64_t t0 = u / US;
     int64_t I = 0;
@@ -344,9 +364,12 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
         u = seg_end;
         if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
             // row segment done: FP64 record of the policy totals
-            const int64_t k = c - sk_owner(p.U, p.ctas, row_start(I, p.nb) * US);
+            const int64_t k = c - range_owner(p.lo, p.ctas, row_start(I, p.nb) * US);
+            // k < K by the bound of sym_sizes; never write past it
+            if (k >= p.K && tid == 0) dev::set_status(p.status, kStatusInvalid);
 #pragma unroll
             for (int kk = 0; kk < IR; ++kk) {
+                if (k >= p.K) break;
                 const int64_t slot = w * 128 + 32 * kk + l;
                 double *r = p.rec + (((I * p.K + k) * BI) + slot) * 4;
                 __stcs(reinterpret_cast<double2 *>(r),
@@ -398,9 +421,10 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
 #pragma unroll
         for (int e = 0; e < 4; ++e) a[e].zero();
         const int64_t rs = row_start(I, p.nb);
-        const int64_t c0 = sk_owner(p.U, p.ctas, rs * US);
-        const int64_t c1 = sk_owner(p.U, p.ctas, (rs + (p.nb - I)) * US - 1);
-        for (int64_t k = 0; k <= c1 - c0; ++k) {
+        const int64_t c0 = range_owner(p.lo, p.ctas, rs * US);
+        const int64_t c1 = range_owner(p.lo, p.ctas, (rs + (p.nb - I)) * US - 1);
+        for (int64_t k = 0; k <= c1 - c0 && k < p.K; ++k) {
+            if (__ldg(p.lo + c0 + k) == __ldg(p.lo + c0 + k + 1)) continue;  // empty range
             const double2 *rr = reinterpret_cast<const double2 *>(p.rec + (((I * p.K + k) * BI) + r) * 4);
             const double2 u = __ldg(rr), v = __ldg(rr + 1);
             add_record<POL>(a[0], u.x);
@@ -434,8 +458,128 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
     if (bad) dev::set_status(status, kStatusNonFinite);
 }
 
+// ------------------------------------------------ cost-weighted stream-K
+// Relative cost of one (warp, j-set) of an item.  Far pairs: the FP32 pipe
+// cycles per lane and step (off-diagonal 18, diagonal i-side only 13).  Near
+// pairs take 24 / 19 pipe cycles, but a near j-set of one warp also holds
+// its 15 siblings at the next barrier; weighted 36 / 28 the per-CTA timers
+// of a 2^20 Plummer evaluation end within 1 % of each other (24 / 19: the
+// last CTA 3.5 % after the median).
+constexpr uint32_t kCostSymFar = 18, kCostSymNear = 36, kCostDiagFar = 13, kCostDiagNear = 28;
+constexpr uint32_t kUnitCostMin = KB * NW * kCostDiagFar;
+constexpr uint32_t kUnitCostMax = KB * NW * kCostSymNear;
+
+__device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64_t &J) {
+    const double b = 2.0 * (double)nb + 1.0;
+    int64_t r = (int64_t)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+    if (r < 0) r = 0;
+    if (r > nb - 1) r = nb - 1;
+    while (r > 0 && row_start(r, nb) > t) --r;
+    while (r + 1 < nb && row_start(r + 1, nb) <= t) ++r;
+    I = r;
+    J = r + (t - row_start(r, nb));
+}
+
+// One warp per item: the near/far decisions the pair kernel will take.
+template <int MODE>
+__global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32_t *cost) {
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (t >= p.T) return;  // whole warps
+    int64_t I, J;
+    item_of(t, p.nb, I, J);
+    const bool sym = I != J;
+    const uint32_t cn = sym ? kCostSymNear : kCostDiagNear;
+    const uint32_t cf = sym ? kCostSymFar : kCostDiagFar;
+    uint32_t c = 0;
+    if (MODE != 2) {
+        c = (MODE == 1 ? cn : cf) * 2 * NW;  // this lane's 2 j-sets x 16 warps
+    } else {
+        float tb[2][7];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int a = 0; a < 7; ++a) tb[h][a] = __ldg(p.jbox + (J * BI / JS + l + 32 * h) * 8 + a);
+        for (int w = 0; w < NW; ++w) {
+            float wb[7];
+#pragma unroll
+            for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + ((I * BI + w * 128) / 128) * 8 + a);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) c += boxes_near(wb, tb[h], p.gamma) ? cn : cf;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (l == 0) cost[t] = c;
+}
+
+// prefix[t] = sum of cost[0, t), prefix[T] = total (one block, fixed order).
+__global__ void __launch_bounds__(1024) sym_scan_kernel(const uint32_t *cost, int64_t T,
+                                                        unsigned long long *prefix) {
+    __shared__ unsigned long long part[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (T + 1023) / 1024;
+    const int64_t a = tid * per, b = (a + per) < T ? (a + per) : T;
+    unsigned long long s = 0;
+    for (int64_t t = a; t < b; ++t) s += cost[t];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const unsigned long long v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        prefix[T] = run;
+    }
+    __syncthreads();
+    unsigned long long run = part[tid];
+    for (int64_t t = a; t < b; ++t) {
+        prefix[t] = run;
+        run += cost[t];
+    }
+}
+
+// lo[c] = the unit where the cumulative cost reaches c / ctas of the total
+// (linear inside an item); lo[0] = 0, lo[ctas] = U, non-decreasing.
+__global__ void sym_ranges_kernel(const uint32_t *cost, const unsigned long long *prefix,
+                                  int64_t T, int64_t ctas, int64_t *lo) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ctas;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (c == 0 || c == ctas) {
+            lo[c] = c == 0 ? 0 : T * US;
+            continue;
+        }
+        const unsigned long long target = prefix[T] * (unsigned long long)c / (unsigned long long)ctas;
+        int64_t a = 0, b = T - 1;
+        while (a < b) {
+            const int64_t m = (a + b + 1) / 2;
+            if (prefix[m] <= target)
+                a = m;
+            else
+                b = m - 1;
+        }
+        int64_t off = (int64_t)((target - prefix[a]) * (unsigned long long)US / cost[a]);
+        if (off > US) off = US;
+        lo[c] = a * US + off;
+    }
+}
+
 template <int POL, int MODE>
 int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint32_t *status) {
+    {
+        uint32_t *cost = reinterpret_cast<uint32_t *>(j.ws + j.L.sym_cost);
+        unsigned long long *prefix = reinterpret_cast<unsigned long long *>(
+            j.ws + j.L.sym_cost + align_up(4 * (size_t)p.T, 256));
+        int64_t *lo = const_cast<int64_t *>(p.lo);
+        sym_cost_kernel<MODE><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, cost);
+        sym_scan_kernel<<<1, 1024, 0, j.stream>>>(cost, p.T, prefix);
+        sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(cost, prefix, p.T,
+                                                                                 p.ctas, lo);
+        count_launch(3);
+        NB_CUDA(cudaGetLastError());
+    }
     auto kern = force_sym_kernel<POL, MODE>;
     const size_t smem = kRedBytes + 16 * NT * sizeof(Acc<POL>) +
                         (POL == NB_PREC_F64ACC ? 16 * NT * sizeof(float) : 0);
@@ -471,16 +615,20 @@ SymSizes sym_sizes(int64_t Np) {
     z.T = z.nb * (z.nb + 1) / 2;
     z.U = z.T * US;
     z.ctas = std::min<int64_t>(device_sm_count(), z.U);
-    int64_t K = 1;
-    for (int64_t I = 0; I < z.nb; ++I) {
-        const int64_t rs = row_start(I, z.nb);
-        const int64_t k = sk_owner(z.U, z.ctas, (rs + (z.nb - I)) * US - 1) -
-                          sk_owner(z.U, z.ctas, rs * US) + 1;
-        K = std::max(K, k);
-    }
+    // Records per row: a cost-balanced range holds at least
+    // (U / ctas) * (min unit cost / max unit cost) - 2 units, so a row of
+    // nb * US units meets at most that many ranges plus 2; with short ranges
+    // (empty ones possible) every CTA gets a slot.
+    const double min_len =
+        (double)z.U / (double)z.ctas * (double)kUnitCostMin / (double)kUnitCostMax - 2.0;
+    int64_t K = z.ctas;
+    if (min_len >= 1.0)
+        K = std::min<int64_t>(z.ctas, (int64_t)std::ceil((double)(z.nb * US) / min_len) + 2);
     z.K = K;
     z.p_bytes = (size_t)(z.nb * (z.nb - 1) / 2) * kSymBlock * 16;
     z.rec_bytes = (size_t)z.nb * (size_t)K * kSymBlock * 32;
+    z.cost_bytes = align_up(4 * (size_t)z.T, 256) + align_up(8 * (size_t)(z.T + 1), 256) +
+                   8 * (size_t)(z.ctas + 1);
     return z;
 }
 
@@ -505,8 +653,11 @@ int launch_force_sym(const ForceJob &j, bool adaptive) {
     p.wbox = adaptive ? sort_block_boxes(sb, j.L) : nullptr;
     p.P = reinterpret_cast<float *>(j.ws + j.L.sym_p);
     p.rec = reinterpret_cast<double *>(j.ws + j.L.sym_rec);
+    p.lo = reinterpret_cast<const int64_t *>(j.ws + j.L.sym_cost + align_up(4 * (size_t)z.T, 256) +
+                                             align_up(8 * (size_t)(z.T + 1), 256));
     const int *perm = adaptive ? sort_perm(sb, j.L) : nullptr;
     uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
+    p.status = status;
     const int mode = adaptive ? 2 : (j.split ? 1 : 0);
     switch (j.precision) {
         case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, mode, perm, status);
