@@ -282,7 +282,8 @@ void nb_opts_default(nb_opts *o) {
 }
 
 const char *nb_version(void) {
-    return "nbody-gb300 1.0 (sm_103a; FP32 pairs with FP32/Kahan/FP64 accumulation, FP64 pairs)";
+    return "nbody-gb300 1.1 (sm_103a; FP32 pairs, direct or symmetric (each unordered pair "
+           "once), with FP32/Kahan/FP64 accumulation; FP64 pairs)";
 }
 
 const char *nb_last_error(void) { return g_err; }
