@@ -135,8 +135,18 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
         L.sym_cost = off;
         off = align256(off + z.cost_bytes);
     }
+    if (bsym_wanted(opts, N, B)) {
+        L.bsym = off;
+        L.bsym_bytes = bsym_layout(N, B).bytes;
+        off = align256(off + L.bsym_bytes);
+    }
     L.total = off;
     return L;
+}
+
+bool bsym_wanted(const nb_opts *o, int64_t N, int32_t B) {
+    (void)N;
+    return o && B > 1 && o->precision != NB_PREC_FP64 && o->pairs != NB_PAIRS_DIRECT;
 }
 
 bool sym_wanted(const nb_opts *o, int64_t N, int32_t B) {
@@ -350,6 +360,7 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.threads = o->tune ? o->tune->threads : 0;
     j.positions = o->positions;
     j.gamma = o->near_gamma;
+    j.sym = bsym_wanted(o, N, B);
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)ws;
@@ -378,6 +389,7 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
     j.threads = o->tune ? o->tune->threads : 0;
     j.positions = o->positions;
     j.gamma = o->near_gamma;
+    j.sym = bsym_wanted(o, s->N, s->B);
     j.timeout = timeout_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)s->ws;

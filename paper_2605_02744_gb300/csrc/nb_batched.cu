@@ -630,6 +630,7 @@ static int launch_batched_pol(const BatchedParams &p, int cs, int bt, cudaStream
 int launch_batched(const BatchedJob &j) {
     if (j.precision == NB_PREC_FP64)
         return fail(NB_ERR_UNSUPPORTED, "the batched path computes FP32 pairs (FP32, KAHAN, F64ACC)");
+    if (j.sym) return launch_batched_sym(j);
     if (j.B > kBMaxSlots * 1024) return fail(NB_ERR_UNSUPPORTED, "too many clusters");
     BatchedParams p;
     p.mass = j.mass;

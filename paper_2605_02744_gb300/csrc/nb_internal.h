@@ -68,6 +68,7 @@ struct WsLayout {
     size_t sym_p;     // symmetric-pair path: FP32 j-side partials per block pair
     size_t sym_rec;   // symmetric-pair path: FP64 i-side records per row segment
     size_t sym_cost;  // symmetric-pair path: item costs, their prefix, CTA ranges
+    size_t bsym, bsym_bytes;  // batched symmetric-pair path (0 bytes: not provisioned)
     size_t sym_p_bytes, sym_rec_bytes;  // 0 when the path is not provisioned
     size_t total;
     int64_t Np;       // padded particle count of the pack arrays
@@ -275,6 +276,7 @@ struct BatchedJob {
     int threads;      // threads per CTA (0 = default)
     int positions;    // nb_positions: SPLIT = hi/lo everywhere, else adaptive
     float gamma;      // near/far threshold (0 = default)
+    bool sym;         // symmetric pairs (nb_pairs resolved)
     long long timeout;
     cudaStream_t stream;
     char *ws;
@@ -282,5 +284,16 @@ struct BatchedJob {
 };
 int launch_batched(const BatchedJob &job);
 size_t batched_scratch_bytes(int32_t B);
+
+// Batched symmetric-pair path (nb_sym.cu): the workspace region's layout for
+// N particles in B systems (bounds from N and B only).
+struct BsymLayout {
+    int64_t Ns, blocks, items, pairs;
+    size_t o_sbase, o_ibase, o_pbase, o_rstart, o_bsys, o_items, o_order, o_misc, o_soa, o_perm,
+        o_box32, o_box128, o_P, o_rec, bytes;
+};
+BsymLayout bsym_layout(int64_t N, int32_t B);
+bool bsym_wanted(const nb_opts *opts, int64_t N, int32_t B);
+int launch_batched_sym(const BatchedJob &job);
 
 }  // namespace nb
