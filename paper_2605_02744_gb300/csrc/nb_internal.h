@@ -290,7 +290,7 @@ size_t batched_scratch_bytes(int32_t B);
 struct BsymLayout {
     int64_t Ns, blocks, items, pairs;
     size_t o_sbase, o_ibase, o_pbase, o_rstart, o_bsys, o_items, o_order, o_misc, o_soa, o_perm,
-        o_box32, o_box128, o_P, o_rec, bytes;
+        o_box32, o_box128, o_P, o_rec, o_st0, o_st1, o_pots, bytes;
 };
 BsymLayout bsym_layout(int64_t N, int32_t B);
 bool bsym_wanted(const nb_opts *opts, int64_t N, int32_t B);

@@ -406,6 +406,40 @@ __device__ __forceinline__ void add_record<NB_PREC_F64ACC>(Acc<NB_PREC_F64ACC> &
     a.s += v;
 }
 
+// Adds `count` FP32 partials (stride `stride` float4s) in order.  F64ACC adds
+// groups of 8 in FP32 first (8 x 128 or 8 x 2048 pair terms, the size of one
+// direct-kernel tile of FP32 sums) and each group's sum in FP64: FP64 adds are
+// slow on this part and one per partial made the fold FP64-bound.
+template <int POL>
+__device__ __forceinline__ void add_partials(Acc<POL> (&a)[4], const float4 *P4, int64_t count,
+                                             int64_t stride) {
+    if (POL == NB_PREC_F64ACC) {
+        for (int64_t k0 = 0; k0 < count; k0 += 8) {
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int64_t k1 = (k0 + 8) < count ? (k0 + 8) : count;
+            for (int64_t k = k0; k < k1; ++k) {
+                const float4 v = __ldcs(P4 + k * stride);
+                g.x += v.x;
+                g.y += v.y;
+                g.z += v.z;
+                g.w += v.w;
+            }
+            a[0].add(g.x);
+            a[1].add(g.y);
+            a[2].add(g.z);
+            a[3].add(g.w);
+        }
+    } else {
+        for (int64_t k = 0; k < count; ++k) {
+            const float4 v = __ldcs(P4 + k * stride);
+            a[0].add(v.x);
+            a[1].add(v.y);
+            a[2].add(v.z);
+            a[3].add(v.w);
+        }
+    }
+}
+
 template <int POL>
 __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_t N,
                                                        const int *__restrict__ perm, double G,
@@ -432,14 +466,8 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
             add_record<POL>(a[2], v.x);
             add_record<POL>(a[3], v.y);
         }
-        const float4 *P4 = reinterpret_cast<const float4 *>(p.P) + (I * (I - 1) / 2) * BI + r;
-        for (int64_t i2 = 0; i2 < I; ++i2) {
-            const float4 v = __ldcs(P4 + i2 * BI);
-            a[0].add(v.x);
-            a[1].add(v.y);
-            a[2].add(v.z);
-            a[3].add(v.w);
-        }
+        add_partials<POL>(a, reinterpret_cast<const float4 *>(p.P) + (I * (I - 1) / 2) * BI + r, I,
+                          BI);
         const double ph = a[3].value();
         const double ax = G * a[0].value(), ay = G * a[1].value(), az = G * a[2].value();
         const double gp = -G * ph;
@@ -651,7 +679,17 @@ struct BsParams {
     int64_t items_cap, pairs_cap;
     float gamma;
     uint32_t *status;
+    // FP64 state in slot order for the whole call (contiguous kick, drift,
+    // pack and fold): two buffers of 10 arrays [Ns] (x y z vx vy vz ax ay az m)
+    // -- a re-sort permutes one into the other -- and the potential
+    double *st[2];
+    double *pots;
+    int cur;
 };
+
+__device__ __forceinline__ double *st_arr(const BsParams &p, int b, int k) {
+    return p.st[b] + (int64_t)k * p.Ns;
+}
 
 __device__ __forceinline__ int64_t bs_items_of_row(int64_t nblk, int64_t a) {
     return (nblk - a + BG - 1) / BG;
@@ -748,9 +786,14 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
 }
 
 // Morton order of each system (one CTA per system): FP64 bounding box,
-// 30-bit codes, keys code << 13 | local index, shared-memory bitonic sort.
-__global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p) {
-    extern __shared__ unsigned long long keys[];  // kBsMaxN
+// 30-bit codes, keys code << 13 | source index, shared-memory bitonic sort;
+// then the state is gathered into the other buffer in the new order: from
+// the caller's arrays (from_user: particle order) or from the current
+// slot-order buffer (a re-sort).  The real particles of a system always fill
+// its first n slots; the padding slots hold zeros and perm = -1.
+__global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p, int from_user) {
+    extern __shared__ unsigned long long keys[];  // kBsMaxN keys, then kBsMaxN old perm entries
+    int *old_perm = reinterpret_cast<int *>(keys + kBsMaxN);
     __shared__ double red[6][16];
     const int c = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -758,11 +801,15 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p) {
     if (ns == 0) return;
     const int64_t o0 = p.offsets[c];
     const int n = (int)(p.offsets[c + 1] - o0);
+    const int src = p.cur, dst = 1 - p.cur;
+    auto xsrc = [&](int e, int d) -> double {
+        return from_user ? p.pos[3 * (o0 + e) + d] : st_arr(p, src, d)[sb + e];
+    };
     double lo[3] = {1e308, 1e308, 1e308}, hi[3] = {-1e308, -1e308, -1e308};
     for (int e = tid; e < n; e += blockDim.x)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double x = p.pos[3 * (o0 + e) + d];
+            const double x = xsrc(e, d);
             lo[d] = fmin(lo[d], x);
             hi[d] = fmax(hi[d], x);
         }
@@ -778,6 +825,8 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p) {
             red[d][w] = lo[d];
             red[3 + d][w] = hi[d];
         }
+    if (!from_user)
+        for (int e = tid; e < n; e += blockDim.x) old_perm[e] = p.perm[sb + e];
     __syncthreads();
     double blo[3], scale[3];
 #pragma unroll
@@ -798,7 +847,7 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p) {
             uint32_t code = 0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double q = (p.pos[3 * (o0 + e) + d] - blo[d]) * scale[d];
+                double q = (xsrc(e, d) - blo[d]) * scale[d];
                 q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
                 uint32_t v = (uint32_t)q, r = 0;
 #pragma unroll
@@ -825,12 +874,57 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p) {
             }
             __syncthreads();
         }
-    for (int64_t s = tid; s < ns; s += blockDim.x)
-        p.perm[sb + s] = s < n ? (int)(o0 + (int64_t)(keys[s] & 0x1fffull)) : -1;
+    for (int64_t s = tid; s < ns; s += blockDim.x) {
+        double v[10];
+        int pi = -1;
+        if (s < n) {
+            const int e = (int)(keys[s] & 0x1fffull);
+            if (from_user) {
+                const int64_t i = o0 + e;
+                pi = (int)i;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    v[d] = p.pos[3 * i + d];
+                    v[3 + d] = p.vel ? p.vel[3 * i + d] : 0.0;
+                    v[6 + d] = p.acc[3 * i + d];
+                }
+                v[9] = p.mass[i];
+            } else {
+                pi = old_perm[e];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) v[k] = st_arr(p, src, k)[sb + e];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) v[k] = 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) st_arr(p, dst, k)[sb + s] = v[k];
+        p.perm[sb + s] = pi;
+    }
+}
+
+// End of a call: the slot-order state back to the caller's arrays.
+__global__ void __launch_bounds__(256) bsym_scatter_kernel(BsParams p, int moved) {
+    const int64_t ns = __ldg(p.totals);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int i = p.perm[s];
+        if (i < 0) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (moved) {
+                p.pos[3 * (int64_t)i + d] = st_arr(p, p.cur, d)[s];
+                p.vel[3 * (int64_t)i + d] = st_arr(p, p.cur, 3 + d)[s];
+            }
+            p.acc[3 * (int64_t)i + d] = st_arr(p, p.cur, 6 + d)[s];
+        }
+        if (p.pot) p.pot[i] = p.pots[s];
+    }
 }
 
 // One block per 128-slot block: optional kick (v += kick a) and drift
-// (x += dt v) of the block's particles (FP64 state), the hi/lo pack, and the
+// (x += dt v) of the block's particles (slot-order FP64 state), the hi/lo pack, and the
 // boxes of its four 32-slot j-sets and of the whole block (real slots only).
 __global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, double dt) {
     const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
@@ -840,17 +934,17 @@ __global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, 
     if (i >= 0) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double x = p.pos[3 * (int64_t)i + d];
+            double x = st_arr(p, p.cur, d)[s];
             if (dt != 0.0) {
-                const double v = p.vel[3 * (int64_t)i + d] + kick * p.acc[3 * (int64_t)i + d];
+                const double v = st_arr(p, p.cur, 3 + d)[s] + kick * st_arr(p, p.cur, 6 + d)[s];
                 x += dt * v;
-                p.vel[3 * (int64_t)i + d] = v;
-                p.pos[3 * (int64_t)i + d] = x;
+                st_arr(p, p.cur, 3 + d)[s] = v;
+                st_arr(p, p.cur, d)[s] = x;
             }
             hi[d] = __double2float_rn(x);
             lo[d] = __double2float_rn(x - (double)hi[d]);
         }
-        m = __double2float_rn(p.mass[i]);
+        m = __double2float_rn(st_arr(p, p.cur, 9)[s]);
     }
     store_packed(p.soa, p.Ns, s, hi, lo, m);
     // boxes
@@ -1006,8 +1100,7 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
     uint32_t bad = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const int i = p.perm[s];
-        if (i < 0) continue;
+        if (p.perm[s] < 0) continue;
         const int64_t blk = s / BW, r = s % BW;
         const int c = p.bsys[blk];
         const int64_t a = blk - p.sbase[c] / BW;
@@ -1022,26 +1115,21 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
             add_record<POL>(acc4[2], v.x);
             add_record<POL>(acc4[3], v.y);
         }
-        const float4 *P4 = reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r;
-        for (int64_t a2 = 0; a2 < a; ++a2) {
-            const float4 v = __ldcs(P4 + a2 * BW);
-            acc4[0].add(v.x);
-            acc4[1].add(v.y);
-            acc4[2].add(v.z);
-            acc4[3].add(v.w);
-        }
+        add_partials<POL>(acc4,
+                          reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r,
+                          a, BW);
         const double ax = p.G * acc4[0].value(), ay = p.G * acc4[1].value(),
                      az = p.G * acc4[2].value();
         const double gp = -p.G * acc4[3].value();
-        p.acc[3 * (int64_t)i] = ax;
-        p.acc[3 * (int64_t)i + 1] = ay;
-        p.acc[3 * (int64_t)i + 2] = az;
+        st_arr(p, p.cur, 6)[s] = ax;
+        st_arr(p, p.cur, 7)[s] = ay;
+        st_arr(p, p.cur, 8)[s] = az;
         if (kick != 0.0) {
-            p.vel[3 * (int64_t)i] += kick * ax;
-            p.vel[3 * (int64_t)i + 1] += kick * ay;
-            p.vel[3 * (int64_t)i + 2] += kick * az;
+            st_arr(p, p.cur, 3)[s] += kick * ax;
+            st_arr(p, p.cur, 4)[s] += kick * ay;
+            st_arr(p, p.cur, 5)[s] += kick * az;
         }
-        if (p.pot) p.pot[i] = gp;
+        p.pots[s] = gp;
         if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
     }
     if (bad) dev::set_status(p.status, kStatusNonFinite);
@@ -1053,11 +1141,14 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     const unsigned pack_grid = (unsigned)nb_max;
     const unsigned fold_grid = (unsigned)std::min<int64_t>(cdiv(nb_max * BW, 256), 64 * (int64_t)device_sm_count());
     const unsigned item_grid = (unsigned)device_sm_count();
+    constexpr int sort_smem = 12 * kBsMaxN;  // keys and the old permutation
     static const cudaError_t optin = cudaFuncSetAttribute(
-        bsym_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kBsMaxN));
+        bsym_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
     NB_CUDA(optin);
-    auto sort = [&]() {
-        bsym_sort_kernel<<<(unsigned)p.B, 512, 8 * kBsMaxN, st>>>(p);
+    p.cur = 0;
+    auto sort = [&](int from_user) {
+        bsym_sort_kernel<<<(unsigned)p.B, 512, sort_smem, st>>>(p, from_user);
+        p.cur ^= 1;
         count_launch();
     };
     constexpr int IPOL = POL == NB_PREC_F64ACC ? NB_PREC_FP32 : POL;
@@ -1072,18 +1163,20 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     };
     bsym_setup_kernel<<<1, 1024, 0, st>>>(p, j.N);
     count_launch();
-    sort();
+    sort(1);
     if (!j.acc_valid || j.nsteps == 0) {
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.0, 0.0);
         count_launch();
         force(0.0);
     }
     for (int64_t n = 0; n < j.nsteps; ++n) {
-        if (n > 0 && n % kBsResort == 0) sort();
+        if (n > 0 && n % kBsResort == 0) sort(0);
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.5 * j.dt, j.dt);
         count_launch();
         force(0.5 * j.dt);
     }
+    bsym_scatter_kernel<<<fold_grid, 256, 0, st>>>(p, j.nsteps > 0 ? 1 : 0);
+    count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -1185,6 +1278,9 @@ BsymLayout bsym_layout(int64_t N, int32_t B) {
     z.o_box128 = take(32 * (size_t)z.blocks);
     z.o_P = take(16 * (size_t)BW * z.pairs);
     z.o_rec = take(32 * (size_t)BW * z.items);
+    z.o_st0 = take(80 * (size_t)z.Ns);
+    z.o_st1 = take(80 * (size_t)z.Ns);
+    z.o_pots = take(8 * (size_t)z.Ns);
     z.bytes = off;
     return z;
 }
@@ -1219,6 +1315,10 @@ int launch_batched_sym(const BatchedJob &j) {
     p.box128 = reinterpret_cast<float *>(base + z.o_box128);
     p.P = reinterpret_cast<float *>(base + z.o_P);
     p.rec = reinterpret_cast<double *>(base + z.o_rec);
+    p.st[0] = reinterpret_cast<double *>(base + z.o_st0);
+    p.st[1] = reinterpret_cast<double *>(base + z.o_st1);
+    p.pots = reinterpret_cast<double *>(base + z.o_pots);
+    p.cur = 0;
     p.items_cap = z.items;
     p.pairs_cap = z.pairs;
     p.gamma = j.gamma > 0.f ? j.gamma : kNearFarGamma;
