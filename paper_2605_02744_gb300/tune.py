@@ -28,7 +28,7 @@ FORCE_CANDIDATES = [
                          (256, 4, 256, 3), (128, 2, 128, 3), (128, 1, 64, 2)]
     for c in (1, 2, 4)
 ]
-BATCHED_CANDIDATES = [dict(cluster_ctas=c, threads=t) for c in (4, 8) for t in (256, 512)]
+BATCHED_CANDIDATES = [dict(cluster_ctas=c, threads=t) for c in (2, 4, 8) for t in (256, 512)]
 VJP_CANDIDATES = [
     dict(threads=t, i_per_thread=i, tile_j=j, stages=s, ctas_per_sm=4)
     for (t, i, j, s) in [(128, 2, 128, 3), (256, 2, 128, 3), (256, 1, 128, 3), (128, 1, 64, 2)]
@@ -132,13 +132,18 @@ def autotune_forces(pos, mass, eps: float, precision="kahan", reps: int = 5, war
 def autotune_batched(pos, vel, mass, offsets, eps, dt: float, nsteps: int = 20,
                      precision="f64acc", reps: int = 3, candidates=None,
                      store: bool = True) -> dict:
-    """Time nsteps batched KDK steps per cluster size; returns the best nb_tune dict."""
+    """Time nsteps batched KDK steps per cluster size; returns the best nb_tune dict.
+
+    The candidates are shapes of the direct batched kernel (NB_PAIRS_DIRECT),
+    which is what is timed; the symmetric batched path has no shape
+    parameters.
+    """
     from .api import System
     n = mass.shape[0]
     results = []
     for cand in candidates or BATCHED_CANDIDATES:
         sysm = System(pos, vel, mass, eps, offsets=offsets, precision=precision, tune=cand,
-                      device=pos.device if torch.is_tensor(pos) else "cuda")
+                      device=pos.device if torch.is_tensor(pos) else "cuda", pairs="direct")
         sysm.step(dt, 1)
         t = _median_ms(lambda: sysm.step(dt, nsteps), reps)
         results.append((t, _cost(cand), cand))

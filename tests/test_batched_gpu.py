@@ -1,11 +1,14 @@
-"""GPU parity of the batched persistent path (many independent clusters).
+"""GPU parity of the batched paths (many independent clusters).
 
-nb_forces_batched against the oracle cluster by cluster (sizes from 1 to the
-8192 maximum, every compiled thread-block-cluster size), nb_step on a batch
-against the oracle's leapfrog per cluster, the 512-cluster workload on a
-sample of clusters (smallest and largest included) for 10 steps and on
-small clusters for the full 1000 steps with the energy-drift gate, device
-rejection of an invalid cluster, bitwise determinism and graph replay.
+Two paths: the default symmetric-pair path (each unordered pair of a cluster
+once, warp-granular work items, per-cluster Morton order) and the persistent
+direct-pair kernel (NB_PAIRS_DIRECT, every compiled thread-block-cluster
+size).  nb_forces_batched against the oracle cluster by cluster (sizes from
+1 to the 8192 maximum), nb_step on a batch against the oracle's leapfrog per
+cluster (across a Morton re-sort), the 512-cluster workload on a sample of
+clusters (smallest and largest included) for 10 steps and on small clusters
+for the full 1000 steps with the energy-drift gate, device rejection of an
+invalid cluster, bitwise determinism and graph replay.
 """
 import numpy as np
 import pytest
@@ -37,12 +40,15 @@ def _eps(b, seed=0):
 
 
 @pytest.mark.parametrize("prec", ["f64acc", "kahan"])
-@pytest.mark.parametrize("cs", [2, 4, 8])
-@pytest.mark.parametrize("bt", [256, 512])
-def test_forces_batched_per_cluster(prec, cs, bt):
+@pytest.mark.parametrize("cs,bt,pairs", [(2, 256, "direct"), (4, 256, "direct"),
+                                         (8, 256, "direct"), (2, 512, "direct"),
+                                         (4, 512, "direct"), (8, 512, "direct"),
+                                         (0, 0, "symmetric")])
+def test_forces_batched_per_cluster(prec, cs, bt, pairs):
     s = _batch(SIZES)
     eps = _eps(len(SIZES))
-    opts = binding.make_opts(prec, tune={"cluster_ctas": cs, "threads": bt})
+    tune = {"cluster_ctas": cs, "threads": bt} if cs else None
+    opts = binding.make_opts(prec, tune=tune, pairs=pairs)
     n = s.n
     acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     pot = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -58,14 +64,17 @@ def test_forces_batched_per_cluster(prec, cs, bt):
         assert rel_err(p[lo:hi], rp).max() <= TOL[prec], (c, SIZES[c])
 
 
-@pytest.mark.parametrize("positions", ["default", "split"])
-def test_step_batched_matches_oracle_per_cluster(positions):
+@pytest.mark.parametrize("positions", ["default", "split", "single"])
+@pytest.mark.parametrize("pairs", ["default", "direct"])
+def test_step_batched_matches_oracle_per_cluster(positions, pairs):
     # 20 steps cross one Morton re-sort of every cluster (every 16 steps)
+    if positions == "single" and pairs == "direct":
+        pytest.skip("the direct batched kernel takes hi/lo or adaptive displacements")
     sizes = [64, 65, 200, 1000, 3000, 7, 1, 8192]
     s = _batch(sizes, seed=3)
     eps = _eps(len(sizes), 1)
     g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc",
-                   positions=positions)
+                   positions=positions, pairs=pairs)
     g.step(1e-3, 20)
     assert g.poll() == binding.NB_OK
     x, v = host(g.pos), host(g.vel)
@@ -83,12 +92,13 @@ def _cluster_energy(x, v, m, pot):
     return 0.5 * (m * (v * v).sum(1)).sum() + 0.5 * (m * pot).sum()
 
 
-def test_workload_512_clusters_sampled():
+@pytest.mark.parametrize("pairs", ["default", "direct"])
+def test_workload_512_clusters_sampled(pairs):
     s = ics.batched_plummer(512, seed=1)
     sizes = np.diff(s.offsets)
     eps = np.full(512, 0.01)
     g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc",
-                   tune={"cluster_ctas": 8})
+                   tune={"cluster_ctas": 8}, pairs=pairs)
     g.step(1e-3, 10)
     assert g.poll() == binding.NB_OK
     x = host(g.pos)
@@ -131,11 +141,12 @@ def test_workload_1000_steps_energy_drift_small_clusters():
         assert d_gpu <= max(2 * d_ref, d_ref + 1e-6), (c, d_gpu, d_ref)
 
 
-def test_invalid_cluster_is_rejected_on_device():
+@pytest.mark.parametrize("pairs", ["default", "direct"])
+def test_invalid_cluster_is_rejected_on_device(pairs):
     sizes = [10, 20, 30]
     s = _batch(sizes)
     eps = np.array([0.01, -1.0, 0.01])  # cluster 1 invalid
-    opts = binding.make_opts("f64acc")
+    opts = binding.make_opts("f64acc", pairs=pairs)
     acc = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
     ws = binding.workspace(s.n, 3, opts)
     binding.nb_forces_batched(dev(s.pos), dev(s.mass), torch.tensor(s.offsets, device="cuda"),
@@ -148,16 +159,35 @@ def test_invalid_cluster_is_rejected_on_device():
     assert binding.nb_poll_status(ws, opts) == binding.NB_OK  # cleared
 
 
-def test_batched_determinism_and_graph_replay():
+@pytest.mark.parametrize("pairs", ["default", "direct"])
+def test_batched_determinism_and_graph_replay(pairs):
     sizes = [500, 64, 2000, 129]
     s = _batch(sizes, seed=9)
     eps = _eps(4, 2)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        a = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, stream=st)
-        b = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, stream=st, use_graph=True)
+        a = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, stream=st, pairs=pairs)
+        b = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, stream=st, use_graph=True,
+                       pairs=pairs)
         for _ in range(2):
             a.step(1e-3, 7)
             b.step(1e-3, 7)
     st.synchronize()
     assert torch.equal(a.pos, b.pos) and torch.equal(a.vel, b.vel) and torch.equal(a.acc, b.acc)
+
+
+def test_symmetric_and_direct_batched_paths_agree():
+    sizes = [8192, 4000, 1, 2, 300, 129, 5000]
+    s = _batch(sizes, seed=11)
+    eps = _eps(len(sizes), 3)
+    out = {}
+    for pairs in ("default", "direct"):
+        g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="kahan",
+                       pairs=pairs)
+        g.step(1e-3, 5)
+        assert g.poll() == binding.NB_OK
+        out[pairs] = (host(g.pos), host(g.acc), host(g.pot))
+    dx = np.abs(out["direct"][0] - s.pos).max()
+    assert np.abs(out["default"][0] - out["direct"][0]).max() <= 1e-5 * dx
+    assert rel_vec_err(out["default"][1], out["direct"][1]).max() <= 2e-5
+    assert rel_err(out["default"][2], out["direct"][2]).max() <= 2e-5
