@@ -93,8 +93,13 @@ typedef enum {
  * needs eps > 0 and a workspace of about N^2 / 256 bytes for the j-side
  * partial sums (4.3 GB at N = 2^20), which nb_workspace_bytes includes when
  * the path is in use.  DEFAULT takes SYMMETRIC for 32768 <= N <= 2^21 and
- * eps > 0, DIRECT otherwise.  Results of both are deterministic; they
- * differ from each other by summation order only. */
+ * eps > 0, DIRECT otherwise.  For batches (B > 1, nb_forces_batched and
+ * nb_step with offsets) DEFAULT and SYMMETRIC take the symmetric batched
+ * path (warp-granular work items; workspace about 250 B per particle plus
+ * 2 KiB per pair of 128-particle blocks of a cluster: 0.9 GB for 512
+ * clusters of up to 8192) and DIRECT the persistent direct-pair kernel
+ * (nb_tune's cluster_ctas / threads).  Results of both are deterministic;
+ * they differ from each other by summation order only. */
 typedef enum {
     NB_PAIRS_DEFAULT = 0,
     NB_PAIRS_DIRECT = 1,
