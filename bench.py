@@ -130,7 +130,7 @@ class ClockSampler:
 def _kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("nb_sym.cu", "nb_device.cuh"):
+    for f in ("nb_sym.cu", "nb_sym_core.cuh", "nb_device.cuh"):
         with open(os.path.join(ROOT, "paper_2605_02744_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

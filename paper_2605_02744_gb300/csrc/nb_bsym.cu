@@ -1,0 +1,658 @@
+// Batches of independent systems with symmetric pairs (see the comment at
+// the top of the batched section below); the pair evaluation is the one of
+// nb_sym.cu (nb_sym_core.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+#include "nb_sym_core.cuh"
+
+namespace nb {
+
+namespace {
+
+using namespace symcore;
+
+// ================================================================ batched
+// Many independent systems (offsets [B+1], eps [B]), each unordered pair of
+// a system evaluated once as above, at warp granularity.  Every system is
+// padded to whole 128-slot blocks in Morton order (re-sorted every 16 steps);
+// a work item is (system c, i-block a, j-blocks [b0, b1)) with b0 >= a and at
+// most 8 j-blocks.  Persistent warps take items from an atomic queue ordered
+// largest first; a warp holds its i-block in registers (4 slots per lane),
+// rotates each 32-slot j-set through its lanes (j-side sums travelling with
+// the particle) and writes, per off-diagonal block pair (a, b), the FP32
+// j-side partial of block b's 128 slots, and per item the i-side total as
+// an FP64 record.  A fold adds, per slot and in a fixed order, the records of
+// its row and the partials of the blocks a' < a, so results do not depend on
+// which warp took which item.
+constexpr int BW = 128;           // slots per warp block
+constexpr int BG = 8;             // j-blocks per item at most
+constexpr int kBsMaxN = 8192;     // particles per system (64 blocks)
+constexpr int kBsResort = 16;     // steps between Morton re-sorts
+
+struct BsParams {
+    int32_t B;
+    const int64_t *offsets;
+    const double *eps;
+    double G;
+    const double *mass;
+    double *pos, *vel, *acc, *pot;
+    int64_t *sbase;      // [B + 1] first slot of each system (multiples of 128)
+    int64_t *ibase;      // [B + 1] first item of each system
+    int64_t *pbase;      // [B + 1] first block pair of each system
+    int32_t *rstart;     // [blocks + 1] first item of each row (global block index)
+    int32_t *bsys;       // [blocks] system of each block
+    int4 *items;         // [items] (c, a, b0, b1)
+    int32_t *order;      // [items] largest first
+    unsigned *counter;   // queue head
+    int64_t *totals;     // slots, items, block pairs, blocks
+    float *soa;          // [7][Ns]
+    int64_t Ns;          // slot capacity
+    int *perm;           // [Ns] slot -> particle, -1 for padding
+    float *box32;        // [Ns / 32][8]
+    float *box128;       // [Ns / 128][8]
+    float *P;            // [block pairs][128][4]
+    double *rec;         // [items][128][4]
+    int64_t items_cap, pairs_cap;
+    float gamma;
+    uint32_t *status;
+    // FP64 state in slot order for the whole call (contiguous kick, drift,
+    // pack and fold): two buffers of 10 arrays [Ns] (x y z vx vy vz ax ay az m)
+    // -- a re-sort permutes one into the other -- and the potential
+    double *st[2];
+    double *pots;
+    int cur;
+};
+
+__device__ __forceinline__ double *st_arr(const BsParams &p, int b, int k) {
+    return p.st[b] + (int64_t)k * p.Ns;
+}
+
+__device__ __forceinline__ int64_t bs_items_of_row(int64_t nblk, int64_t a) {
+    return (nblk - a + BG - 1) / BG;
+}
+
+// Validation, padded layout, item list and its largest-first order (one
+// block of 1024 threads; the systems' sizes are fixed for the whole call).
+__global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N) {
+    __shared__ int64_t s_tot[4];
+    __shared__ int32_t cnt[1024][BG];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        if (p.offsets[0] != 0 || p.offsets[p.B] != N) dev::set_status(p.status, kStatusInvalid);
+        // prefix sums over systems (serial: once per call)
+        int64_t sb = 0, ib = 0, pb = 0, blk = 0;
+        for (int c = 0; c < p.B; ++c) {
+            const int64_t n = p.offsets[c + 1] - p.offsets[c];
+            const double e = p.eps[c];
+            int64_t nblk = 0;
+            if (n >= 1 && n <= kBsMaxN && e > 0.0 && isfinite(e))
+                nblk = (n + BW - 1) / BW;
+            else
+                dev::set_status(p.status, kStatusInvalid);
+            p.sbase[c] = sb;
+            p.ibase[c] = ib;
+            p.pbase[c] = pb;
+            int64_t it = 0;
+            for (int64_t a = 0; a < nblk; ++a) {
+                p.rstart[blk + a] = (int32_t)(ib + it);
+                p.bsys[blk + a] = c;
+                it += bs_items_of_row(nblk, a);
+            }
+            sb += nblk * BW;
+            ib += it;
+            pb += nblk * (nblk - 1) / 2;
+            blk += nblk;
+        }
+        p.sbase[p.B] = sb;
+        p.ibase[p.B] = ib;
+        p.pbase[p.B] = pb;
+        p.rstart[blk] = (int32_t)ib;
+        if (sb > p.Ns || ib > p.items_cap || pb > p.pairs_cap) {
+            dev::set_status(p.status, kStatusInvalid);  // cannot happen: bounds of bsym_layout
+            sb = ib = pb = blk = 0;
+            p.sbase[p.B] = 0;
+        }
+        s_tot[0] = sb;
+        s_tot[1] = ib;
+        s_tot[2] = pb;
+        s_tot[3] = blk;
+        p.totals[0] = sb;
+        p.totals[1] = ib;
+        p.totals[2] = pb;
+        p.totals[3] = blk;
+        *p.counter = 0u;
+    }
+    __syncthreads();
+    const int64_t nitems = s_tot[1];
+    if (s_tot[0] == 0) return;
+    // items, one system per thread
+    for (int c = tid; c < p.B; c += blockDim.x) {
+        const int64_t nblk = (p.sbase[c + 1] - p.sbase[c]) / BW;
+        int64_t idx = p.ibase[c];
+        for (int64_t a = 0; a < nblk; ++a)
+            for (int64_t b0 = a; b0 < nblk; b0 += BG)
+                p.items[idx++] = make_int4(c, (int)a, (int)b0, (int)(b0 + BG < nblk ? b0 + BG : nblk));
+    }
+    __syncthreads();
+    // stable counting sort by size (j-blocks), largest first: per-thread
+    // contiguous chunks, counts per size, exclusive prefix in (size desc,
+    // thread) order
+    const int64_t per = (nitems + 1023) / 1024;
+    const int64_t lo = tid * per, hi = (lo + per) < nitems ? (lo + per) : nitems;
+    for (int k = 0; k < BG; ++k) cnt[tid][k] = 0;
+    for (int64_t i = lo; i < hi; ++i) {
+        const int4 it = p.items[i];
+        cnt[tid][it.w - it.z - 1] += 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int32_t run = 0;
+        for (int k = BG - 1; k >= 0; --k)
+            for (int t = 0; t < 1024; ++t) {
+                const int32_t v = cnt[t][k];
+                cnt[t][k] = run;
+                run += v;
+            }
+    }
+    __syncthreads();
+    for (int64_t i = lo; i < hi; ++i) {
+        const int4 it = p.items[i];
+        p.order[cnt[tid][it.w - it.z - 1]++] = (int32_t)i;
+    }
+}
+
+// Morton order of each system (one CTA per system): FP64 bounding box,
+// 30-bit codes, keys code << 13 | source index, shared-memory bitonic sort;
+// then the state is gathered into the other buffer in the new order: from
+// the caller's arrays (from_user: particle order) or from the current
+// slot-order buffer (a re-sort).  The real particles of a system always fill
+// its first n slots; the padding slots hold zeros and perm = -1.
+__global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p, int from_user) {
+    extern __shared__ unsigned long long keys[];  // kBsMaxN keys, then kBsMaxN old perm entries
+    int *old_perm = reinterpret_cast<int *>(keys + kBsMaxN);
+    __shared__ double red[6][16];
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t sb = p.sbase[c], ns = p.sbase[c + 1] - sb;
+    if (ns == 0) return;
+    const int64_t o0 = p.offsets[c];
+    const int n = (int)(p.offsets[c + 1] - o0);
+    const int src = p.cur, dst = 1 - p.cur;
+    auto xsrc = [&](int e, int d) -> double {
+        return from_user ? p.pos[3 * (o0 + e) + d] : st_arr(p, src, d)[sb + e];
+    };
+    double lo[3] = {1e308, 1e308, 1e308}, hi[3] = {-1e308, -1e308, -1e308};
+    for (int e = tid; e < n; e += blockDim.x)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = xsrc(e, d);
+            lo[d] = fmin(lo[d], x);
+            hi[d] = fmax(hi[d], x);
+        }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            red[d][w] = lo[d];
+            red[3 + d][w] = hi[d];
+        }
+    if (!from_user)
+        for (int e = tid; e < n; e += blockDim.x) old_perm[e] = p.perm[sb + e];
+    __syncthreads();
+    double blo[3], scale[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double a = 1e308, b = -1e308;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) {
+            a = fmin(a, red[d][k]);
+            b = fmax(b, red[3 + d][k]);
+        }
+        blo[d] = a;
+        scale[d] = b > a ? 1023.0 / (b - a) : 0.0;
+    }
+    int P2 = 1;
+    while (P2 < n) P2 <<= 1;
+    for (int e = tid; e < P2; e += blockDim.x) {
+        unsigned long long k = ~0ull;
+        if (e < n) {
+            uint32_t code = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double q = (xsrc(e, d) - blo[d]) * scale[d];
+                q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
+                uint32_t v = (uint32_t)q, r = 0;
+#pragma unroll
+                for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
+                code |= r << d;
+            }
+            k = ((unsigned long long)code << 13) | (unsigned long long)e;
+        }
+        keys[e] = k;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int e = tid; e < P2; e += blockDim.x) {
+                const int x = e ^ j;
+                if (x > e) {
+                    const bool asc = (e & k) == 0;
+                    const unsigned long long a = keys[e], b = keys[x];
+                    if ((a > b) == asc) {
+                        keys[e] = b;
+                        keys[x] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int64_t s = tid; s < ns; s += blockDim.x) {
+        double v[10];
+        int pi = -1;
+        if (s < n) {
+            const int e = (int)(keys[s] & 0x1fffull);
+            if (from_user) {
+                const int64_t i = o0 + e;
+                pi = (int)i;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    v[d] = p.pos[3 * i + d];
+                    v[3 + d] = p.vel ? p.vel[3 * i + d] : 0.0;
+                    v[6 + d] = p.acc[3 * i + d];
+                }
+                v[9] = p.mass[i];
+            } else {
+                pi = old_perm[e];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) v[k] = st_arr(p, src, k)[sb + e];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) v[k] = 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) st_arr(p, dst, k)[sb + s] = v[k];
+        p.perm[sb + s] = pi;
+    }
+}
+
+// End of a call: the slot-order state back to the caller's arrays.
+__global__ void __launch_bounds__(256) bsym_scatter_kernel(BsParams p, int moved) {
+    const int64_t ns = __ldg(p.totals);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int i = p.perm[s];
+        if (i < 0) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (moved) {
+                p.pos[3 * (int64_t)i + d] = st_arr(p, p.cur, d)[s];
+                p.vel[3 * (int64_t)i + d] = st_arr(p, p.cur, 3 + d)[s];
+            }
+            p.acc[3 * (int64_t)i + d] = st_arr(p, p.cur, 6 + d)[s];
+        }
+        if (p.pot) p.pot[i] = p.pots[s];
+    }
+}
+
+// One block per 128-slot block: optional kick (v += kick a) and drift
+// (x += dt v) of the block's particles (slot-order FP64 state), the hi/lo pack, and the
+// boxes of its four 32-slot j-sets and of the whole block (real slots only).
+__global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, double dt) {
+    const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
+    if ((int64_t)blockIdx.x * BW >= __ldg(p.totals)) return;  // whole block
+    const int i = p.perm[s];
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f}, m = 0.f;
+    if (i >= 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = st_arr(p, p.cur, d)[s];
+            if (dt != 0.0) {
+                const double v = st_arr(p, p.cur, 3 + d)[s] + kick * st_arr(p, p.cur, 6 + d)[s];
+                x += dt * v;
+                st_arr(p, p.cur, 3 + d)[s] = v;
+                st_arr(p, p.cur, d)[s] = x;
+            }
+            hi[d] = __double2float_rn(x);
+            lo[d] = __double2float_rn(x - (double)hi[d]);
+        }
+        m = __double2float_rn(st_arr(p, p.cur, 9)[s]);
+    }
+    store_packed(p.soa, p.Ns, s, hi, lo, m);
+    // boxes
+    float bl[3], bh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bl[d] = i >= 0 ? hi[d] : 3e38f;
+        bh[d] = i >= 0 ? hi[d] : -3e38f;
+        for (int o = 16; o > 0; o >>= 1) {
+            bl[d] = fminf(bl[d], __shfl_xor_sync(0xffffffffu, bl[d], o));
+            bh[d] = fmaxf(bh[d], __shfl_xor_sync(0xffffffffu, bh[d], o));
+        }
+    }
+    __shared__ float wb[4][6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        float amax = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            p.box32[(s / 32) * 8 + d] = bl[d];
+            p.box32[(s / 32) * 8 + 3 + d] = bh[d];
+            wb[w][d] = bl[d];
+            wb[w][3 + d] = bh[d];
+            amax = fmaxf(amax, fmaxf(fabsf(bl[d]), fabsf(bh[d])));
+        }
+        p.box32[(s / 32) * 8 + 6] = bh[0] < bl[0] ? 0.f : amax;
+        p.box32[(s / 32) * 8 + 7] = 0.f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float l3[3] = {3e38f, 3e38f, 3e38f}, h3[3] = {-3e38f, -3e38f, -3e38f}, amax = 0.f;
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                l3[d] = fminf(l3[d], wb[k][d]);
+                h3[d] = fmaxf(h3[d], wb[k][3 + d]);
+            }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            p.box128[blockIdx.x * 8 + d] = l3[d];
+            p.box128[blockIdx.x * 8 + 3 + d] = h3[d];
+            amax = fmaxf(amax, fmaxf(fabsf(l3[d]), fabsf(h3[d])));
+        }
+        p.box128[blockIdx.x * 8 + 6] = h3[0] < l3[0] ? 0.f : amax;
+        p.box128[blockIdx.x * 8 + 7] = 0.f;
+    }
+}
+
+// Persistent warps over the item queue.
+template <int POL, int MODE>
+__global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
+    // per-warp i-side totals of the current item (FP64 policy: FP32 within
+    // an item of <= 8 blocks, FP64 in the record and the fold)
+    constexpr int IPOL = POL == NB_PREC_F64ACC ? NB_PREC_FP32 : POL;
+    extern __shared__ __align__(16) unsigned char bs_smem[];
+    auto tot = reinterpret_cast<Acc<IPOL>(*)[16][32]>(bs_smem);  // [NW][16][32]
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t nitems = __ldg(p.totals + 1);
+    ISet S;
+    while (true) {
+        unsigned q0 = 0;
+        if (l == 0) q0 = atomicAdd(p.counter, 1u);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if ((int64_t)q0 >= nitems) break;
+        const int idx = __ldg(p.order + q0);
+        const int4 it = p.items[idx];
+        const int c = it.x, a = it.y, b0 = it.z, b1 = it.w;
+        const int64_t sb = p.sbase[c];
+        const int64_t ib = sb + (int64_t)BW * a;
+        const float ef = (float)__ldg(p.eps + c);
+        const float2 e2 = f2(ef * ef, ef * ef);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float v[2][7];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int d = 0; d < 7; ++d) v[h][d] = __ldg(p.soa + d * p.Ns + ib + 32 * (2 * g + h) + l);
+            S.nx[g] = f2(-v[0][0], -v[1][0]);
+            S.ny[g] = f2(-v[0][1], -v[1][1]);
+            S.nz[g] = f2(-v[0][2], -v[1][2]);
+            S.m[g] = f2(v[0][3], v[1][3]);
+            S.nm[g] = f2(-v[0][3], -v[1][3]);
+            S.nxl[g] = f2(-v[0][4], -v[1][4]);
+            S.nyl[g] = f2(-v[0][5], -v[1][5]);
+            S.nzl[g] = f2(-v[0][6], -v[1][6]);
+            S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int v = 0; v < 16; ++v) tot[w][v][l].zero();
+        const int nq = (b1 - b0) * 4;  // j-sets of the item (<= 32)
+        unsigned near = 0u;
+        if (MODE == 2) {
+            float wbx[7], tb[7];
+#pragma unroll
+            for (int d = 0; d < 7; ++d) wbx[d] = __ldg(p.box128 + (ib / BW) * 8 + d);
+            const int64_t js = (sb + (int64_t)BW * b0) / JS + (l < nq ? l : 0);
+#pragma unroll
+            for (int d = 0; d < 7; ++d) tb[d] = __ldg(p.box32 + js * 8 + d);
+            near = __ballot_sync(0xffffffffu, l < nq && boxes_near(wbx, tb, p.gamma));
+        }
+        float jn[7];
+        const int64_t jb0 = sb + (int64_t)BW * b0;
+#pragma unroll
+        for (int d = 0; d < 7; ++d) jn[d] = __ldg(p.soa + d * p.Ns + jb0 + l);
+        for (int q = 0; q < nq; ++q) {
+            float jc[7];
+#pragma unroll
+            for (int d = 0; d < 7; ++d) jc[d] = jn[d];
+            if (q + 1 < nq)
+#pragma unroll
+                for (int d = 0; d < 7; ++d) jn[d] = __ldg(p.soa + d * p.Ns + jb0 + JS * (q + 1) + l);
+            const int b = b0 + (q >> 2);
+            const bool nqb = (near >> q) & 1u;
+            float4 bs;
+            if (b != a) {
+                run_set<MODE, true>(S, e2, jc, nqb, bs, -1);
+                const int64_t pair = p.pbase[c] + (int64_t)b * (b - 1) / 2 + a;
+                __stcs(reinterpret_cast<float4 *>(p.P) + pair * BW + 32 * (q & 3) + l, bs);
+            } else {
+                run_set<MODE, false>(S, e2, jc, nqb, bs, q & 3);
+            }
+            if ((q & 3) == 3) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const float2 v4[4] = {S.ax[g], S.ay[g], S.az[g], S.ph[g]};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        tot[w][(2 * g) * 4 + e][l].add(v4[e].x);
+                        tot[w][(2 * g + 1) * 4 + e][l].add(v4[e].y);
+                    }
+                    S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IR; ++k) {
+            double *r = p.rec + ((int64_t)idx * BW + 32 * k + l) * 4;
+            __stcs(reinterpret_cast<double2 *>(r),
+                   make_double2(tot[w][k * 4 + 0][l].value(), tot[w][k * 4 + 1][l].value()));
+            __stcs(reinterpret_cast<double2 *>(r) + 1,
+                   make_double2(tot[w][k * 4 + 2][l].value(), tot[w][k * 4 + 3][l].value()));
+        }
+    }
+}
+
+// Per slot: the records of its row and the partials of blocks a' < a (fixed
+// order), x G, closing kick, store; resets the queue for the next step.
+template <int POL>
+__global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick) {
+    const int64_t ns = __ldg(p.totals);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0u;
+    uint32_t bad = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (p.perm[s] < 0) continue;
+        const int64_t blk = s / BW, r = s % BW;
+        const int c = p.bsys[blk];
+        const int64_t a = blk - p.sbase[c] / BW;
+        Acc<POL> acc4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc4[e].zero();
+        for (int32_t it = p.rstart[blk]; it < p.rstart[blk + 1]; ++it) {
+            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + ((int64_t)it * BW + r) * 4);
+            const double2 u = __ldcs(rr), v = __ldcs(rr + 1);
+            add_record<POL>(acc4[0], u.x);
+            add_record<POL>(acc4[1], u.y);
+            add_record<POL>(acc4[2], v.x);
+            add_record<POL>(acc4[3], v.y);
+        }
+        add_partials<POL>(acc4,
+                          reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r,
+                          a, BW);
+        const double ax = p.G * acc4[0].value(), ay = p.G * acc4[1].value(),
+                     az = p.G * acc4[2].value();
+        const double gp = -p.G * acc4[3].value();
+        st_arr(p, p.cur, 6)[s] = ax;
+        st_arr(p, p.cur, 7)[s] = ay;
+        st_arr(p, p.cur, 8)[s] = az;
+        if (kick != 0.0) {
+            st_arr(p, p.cur, 3)[s] += kick * ax;
+            st_arr(p, p.cur, 4)[s] += kick * ay;
+            st_arr(p, p.cur, 5)[s] += kick * az;
+        }
+        p.pots[s] = gp;
+        if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
+    }
+    if (bad) dev::set_status(p.status, kStatusNonFinite);
+}
+
+template <int POL, int MODE>
+int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
+    const cudaStream_t st = j.stream;
+    const unsigned pack_grid = (unsigned)nb_max;
+    const unsigned fold_grid = (unsigned)std::min<int64_t>(cdiv(nb_max * BW, 256), 64 * (int64_t)device_sm_count());
+    const unsigned item_grid = (unsigned)device_sm_count();
+    constexpr int sort_smem = 12 * kBsMaxN;  // keys and the old permutation
+    static const cudaError_t optin = cudaFuncSetAttribute(
+        bsym_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
+    NB_CUDA(optin);
+    p.cur = 0;
+    auto sort = [&](int from_user) {
+        bsym_sort_kernel<<<(unsigned)p.B, 512, sort_smem, st>>>(p, from_user);
+        p.cur ^= 1;
+        count_launch();
+    };
+    constexpr int IPOL = POL == NB_PREC_F64ACC ? NB_PREC_FP32 : POL;
+    const size_t item_smem = (size_t)NW * 16 * 32 * sizeof(Acc<IPOL>);
+    static const cudaError_t optin_item = cudaFuncSetAttribute(
+        bsym_item_kernel<POL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)item_smem);
+    NB_CUDA(optin_item);
+    auto force = [&](double kick) {
+        bsym_item_kernel<POL, MODE><<<item_grid, NT, item_smem, st>>>(p);
+        bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, kick);
+        count_launch(2);
+    };
+    bsym_setup_kernel<<<1, 1024, 0, st>>>(p, j.N);
+    count_launch();
+    sort(1);
+    if (!j.acc_valid || j.nsteps == 0) {
+        bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.0, 0.0);
+        count_launch();
+        force(0.0);
+    }
+    for (int64_t n = 0; n < j.nsteps; ++n) {
+        if (n > 0 && n % kBsResort == 0) sort(0);
+        bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.5 * j.dt, j.dt);
+        count_launch();
+        force(0.5 * j.dt);
+    }
+    bsym_scatter_kernel<<<fold_grid, 256, 0, st>>>(p, j.nsteps > 0 ? 1 : 0);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <int POL>
+int launch_bsym_pol(BsParams p, const BatchedJob &j, int mode, int64_t nb_max) {
+    switch (mode) {
+        case 0: return launch_bsym_steps<POL, 0>(p, j, nb_max);
+        case 1: return launch_bsym_steps<POL, 1>(p, j, nb_max);
+        default: return launch_bsym_steps<POL, 2>(p, j, nb_max);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ batched host
+BsymLayout bsym_layout(int64_t N, int32_t B) {
+    BsymLayout z{};
+    z.Ns = round_up(N + (int64_t)BW * B, BW);
+    z.blocks = z.Ns / BW;
+    z.items = 6 * z.blocks;                 // per system <= nblk (1 + 65 / 16) items
+    z.pairs = (int64_t)(BW / 2) * z.blocks;  // per system nblk (nblk - 1) / 2 <= 32 nblk
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    z.o_sbase = take(8 * (size_t)(B + 1));
+    z.o_ibase = take(8 * (size_t)(B + 1));
+    z.o_pbase = take(8 * (size_t)(B + 1));
+    z.o_rstart = take(4 * (size_t)(z.blocks + 1));
+    z.o_bsys = take(4 * (size_t)z.blocks);
+    z.o_items = take(16 * (size_t)z.items);
+    z.o_order = take(4 * (size_t)z.items);
+    z.o_misc = take(256);  // counter, totals
+    z.o_soa = take(4 * (size_t)kPackArrays * z.Ns);
+    z.o_perm = take(4 * (size_t)z.Ns);
+    z.o_box32 = take(32 * (size_t)(z.Ns / 32));
+    z.o_box128 = take(32 * (size_t)z.blocks);
+    z.o_P = take(16 * (size_t)BW * z.pairs);
+    z.o_rec = take(32 * (size_t)BW * z.items);
+    z.o_st0 = take(80 * (size_t)z.Ns);
+    z.o_st1 = take(80 * (size_t)z.Ns);
+    z.o_pots = take(8 * (size_t)z.Ns);
+    z.bytes = off;
+    return z;
+}
+
+int launch_batched_sym(const BatchedJob &j) {
+    if (j.L.bsym_bytes == 0) return fail(NB_ERR_WORKSPACE, "workspace has no batched symmetric buffers");
+    const BsymLayout z = bsym_layout(j.N, j.B);
+    char *base = j.ws + j.L.bsym;
+    BsParams p;
+    p.B = j.B;
+    p.offsets = j.offsets;
+    p.eps = j.eps;
+    p.G = j.G;
+    p.mass = j.mass;
+    p.pos = j.pos;
+    p.vel = j.vel;
+    p.acc = j.acc;
+    p.pot = j.pot;
+    p.sbase = reinterpret_cast<int64_t *>(base + z.o_sbase);
+    p.ibase = reinterpret_cast<int64_t *>(base + z.o_ibase);
+    p.pbase = reinterpret_cast<int64_t *>(base + z.o_pbase);
+    p.rstart = reinterpret_cast<int32_t *>(base + z.o_rstart);
+    p.bsys = reinterpret_cast<int32_t *>(base + z.o_bsys);
+    p.items = reinterpret_cast<int4 *>(base + z.o_items);
+    p.order = reinterpret_cast<int32_t *>(base + z.o_order);
+    p.counter = reinterpret_cast<unsigned *>(base + z.o_misc);
+    p.totals = reinterpret_cast<int64_t *>(base + z.o_misc + 64);
+    p.soa = reinterpret_cast<float *>(base + z.o_soa);
+    p.Ns = z.Ns;
+    p.perm = reinterpret_cast<int *>(base + z.o_perm);
+    p.box32 = reinterpret_cast<float *>(base + z.o_box32);
+    p.box128 = reinterpret_cast<float *>(base + z.o_box128);
+    p.P = reinterpret_cast<float *>(base + z.o_P);
+    p.rec = reinterpret_cast<double *>(base + z.o_rec);
+    p.st[0] = reinterpret_cast<double *>(base + z.o_st0);
+    p.st[1] = reinterpret_cast<double *>(base + z.o_st1);
+    p.pots = reinterpret_cast<double *>(base + z.o_pots);
+    p.cur = 0;
+    p.items_cap = z.items;
+    p.pairs_cap = z.pairs;
+    p.gamma = j.gamma > 0.f ? j.gamma : kNearFarGamma;
+    p.status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
+    const int mode = j.positions == NB_POS_SPLIT ? 1 : (j.positions == NB_POS_SINGLE ? 0 : 2);
+    switch (j.precision) {
+        case NB_PREC_FP32: return launch_bsym_pol<NB_PREC_FP32>(p, j, mode, z.blocks);
+        case NB_PREC_KAHAN: return launch_bsym_pol<NB_PREC_KAHAN>(p, j, mode, z.blocks);
+        case NB_PREC_F64ACC: return launch_bsym_pol<NB_PREC_F64ACC>(p, j, mode, z.blocks);
+    }
+    return fail(NB_ERR_UNSUPPORTED, "symmetric pairs compute FP32 pairs (FP32, KAHAN, F64ACC)");
+}
+
+
+}  // namespace nb
