@@ -72,16 +72,18 @@ namespace {
 
 using namespace symcore;
 
-constexpr int BI = NW * 32 * IR;    // slots per row block
+constexpr int SW = 16;              // warps per CTA of the pair kernel
+constexpr int SNT = SW * 32;        // threads per CTA
+constexpr int CPS = 1;              // resident CTAs per SM
+constexpr int BI = SW * 32 * IR;    // slots per row block
 constexpr int NJS = BI / JS;        // j-sets per block
 constexpr int KB = 4;               // j-sets per cross-warp reduction
 constexpr int FL = 4;               // j-sets per i-side flush of the register sums
 constexpr int FL2 = 16;             // F64ACC: j-sets per flush of the FP32 middle sums
 constexpr int US = NJS / KB;        // stream-K units (KB j-sets) per item
 static_assert(BI == kSymBlock, "row block size");
-static_assert(KB * JS * 4 == NT, "one reduced value per thread");
 static_assert(NJS % KB == 0 && NJS % FL2 == 0 && FL2 % FL == 0, "groups tile a block");
-constexpr size_t kRedBytes = 2 * KB * NW * 32 * sizeof(float4);
+constexpr size_t kRedBytes = 2 * KB * SW * 32 * sizeof(float4);
 
 struct SymParams {
     const float *soa;   // packed SoA [7][Np]
@@ -126,12 +128,12 @@ __device__ __forceinline__ void load_j(const SymParams &p, int64_t s, float (&j)
 
 // MODE: 0 single-float displacement, 1 hi/lo, 2 adaptive.
 template <int POL, int MODE>
-__global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
+__global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *red = reinterpret_cast<float4 *>(smem);                   // [2][KB][NW][32]
-    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smem + kRedBytes);   // [16][NT]
+    float4 *red = reinterpret_cast<float4 *>(smem);                   // [2][KB][SW][32]
+    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smem + kRedBytes);   // [16][SNT]
     constexpr bool MID = POL == NB_PREC_F64ACC;
-    float *mid = reinterpret_cast<float *>(smem + kRedBytes + 16 * NT * sizeof(Acc<POL>));
+    float *mid = reinterpret_cast<float *>(smem + kRedBytes + 16 * SNT * sizeof(Acc<POL>));
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     const int64_t c = blockIdx.x;
     int64_t u = __ldg(p.lo + c);
@@ -170,8 +172,8 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
             }
 #pragma unroll
             for (int v = 0; v < 16; ++v) {
-                tot[v * NT + tid].zero();
-                if (MID) mid[v * NT + tid] = 0.f;
+                tot[v * SNT + tid].zero();
+                if (MID) mid[v * SNT + tid] = 0.f;
             }
             row_open = true;
         }
@@ -183,14 +185,15 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
             float wb[7];
 #pragma unroll
             for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + (ib / 128) * 8 + a);
-            float tb[2][7];
+            static_assert(NJS == 32 || NJS == 64, "one or two 32-bit ballots per block");
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < NJS / 32; ++h) {
+                float tb[7];
 #pragma unroll
-                for (int a = 0; a < 7; ++a) tb[h][a] = __ldg(p.jbox + (jb / JS + l + 32 * h) * 8 + a);
-            const unsigned lo = __ballot_sync(0xffffffffu, boxes_near(wb, tb[0], p.gamma));
-            const unsigned hi = __ballot_sync(0xffffffffu, boxes_near(wb, tb[1], p.gamma));
-            near = ((unsigned long long)hi << 32) | lo;
+                for (int a = 0; a < 7; ++a) tb[a] = __ldg(p.jbox + (jb / JS + l + 32 * h) * 8 + a);
+                const unsigned m = __ballot_sync(0xffffffffu, boxes_near(wb, tb, p.gamma));
+                near |= (unsigned long long)m << (32 * h);
+            }
         }
         const int64_t pidx = J * (J - 1) / 2 + I;
         float jn[7];
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
             float4 b;
             if (sym) {
                 run_set<MODE, true>(S, e2, jc, nq, b, -1);
-                red[((half * KB + (q % KB)) * NW + w) * 32 + l] = b;
+                red[((half * KB + (q % KB)) * SW + w) * 32 + l] = b;
             } else {
                 run_set<MODE, false>(S, e2, jc, nq, b, (q >> 2) == w ? (q & 3) : -1);
             }
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
                     const float2 v4[4] = {S.ax[g], S.ay[g], S.az[g], S.ph[g]};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int v0 = ((2 * g) * 4 + e) * NT + tid;
-                        const int v1 = ((2 * g + 1) * 4 + e) * NT + tid;
+                        const int v0 = ((2 * g) * 4 + e) * SNT + tid;
+                        const int v1 = ((2 * g + 1) * 4 + e) * SNT + tid;
                         if (MID) {
                             mid[v0] += v4[e].x;
                             mid[v1] += v4[e].y;
@@ -229,22 +232,24 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
                 if (MID && ((q + 1) % FL2 == 0 || q + 1 == qb)) {
 #pragma unroll
                     for (int v = 0; v < 16; ++v) {
-                        tot[v * NT + tid].add(mid[v * NT + tid]);
-                        mid[v * NT + tid] = 0.f;
+                        tot[v * SNT + tid].add(mid[v * SNT + tid]);
+                        mid[v * SNT + tid] = 0.f;
                     }
                 }
             }
             if (sym && (q + 1) % KB == 0) {
                 __syncthreads();
-                const int qq = tid >> 7, ll = (tid >> 2) & 31, e = tid & 3;
-                const float *r =
-                    reinterpret_cast<const float *>(red) + ((half * KB + qq) * NW * 32 + ll) * 4 + e;
-                float s = 0.f;
+                for (int v = tid; v < KB * JS * 4; v += SNT) {
+                    const int qq = v >> 7, ll = (v >> 2) & 31, e = v & 3;
+                    const float *r = reinterpret_cast<const float *>(red) +
+                                     ((half * KB + qq) * SW * 32 + ll) * 4 + e;
+                    float s = 0.f;
 #pragma unroll
-                for (int w2 = 0; w2 < NW; ++w2) s += r[w2 * 32 * 4];
-                // streaming store: the partials are read once, by the fold, and must
-                // not evict the packed positions that every CTA re-reads from L2
-                __stcs(p.P + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, s);
+                    for (int w2 = 0; w2 < SW; ++w2) s += r[w2 * 32 * 4];
+                    // streaming store: the partials are read once, by the fold, and
+                    // must not evict the packed positions every CTA re-reads from L2
+                    __stcs(p.P + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, s);
+                }
                 half ^= 1;
             }
         }
@@ -260,11 +265,11 @@ __global__ void __launch_bounds__(NT, 1) force_sym_kernel(const SymParams p) {
                 const int64_t slot = w * 128 + 32 * kk + l;
                 double *r = p.rec + (((I * p.K + k) * BI) + slot) * 4;
                 __stcs(reinterpret_cast<double2 *>(r),
-                       make_double2(tot[(kk * 4 + 0) * NT + tid].value(),
-                                    tot[(kk * 4 + 1) * NT + tid].value()));
+                       make_double2(tot[(kk * 4 + 0) * SNT + tid].value(),
+                                    tot[(kk * 4 + 1) * SNT + tid].value()));
                 __stcs(reinterpret_cast<double2 *>(r) + 1,
-                       make_double2(tot[(kk * 4 + 2) * NT + tid].value(),
-                                    tot[(kk * 4 + 3) * NT + tid].value()));
+                       make_double2(tot[(kk * 4 + 2) * SNT + tid].value(),
+                                    tot[(kk * 4 + 3) * SNT + tid].value()));
             }
             row_open = false;
         }
@@ -329,8 +334,8 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
 // of a 2^20 Plummer evaluation end within 1 % of each other (24 / 19: the
 // last CTA 3.5 % after the median).
 constexpr uint32_t kCostSymFar = 18, kCostSymNear = 36, kCostDiagFar = 13, kCostDiagNear = 28;
-constexpr uint32_t kUnitCostMin = KB * NW * kCostDiagFar;
-constexpr uint32_t kUnitCostMax = KB * NW * kCostSymNear;
+constexpr uint32_t kUnitCostMin = KB * SW * kCostDiagFar;
+constexpr uint32_t kUnitCostMax = KB * SW * kCostSymNear;
 
 __device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64_t &J) {
     const double b = 2.0 * (double)nb + 1.0;
@@ -356,19 +361,20 @@ __global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32
     const uint32_t cf = sym ? kCostSymFar : kCostDiagFar;
     uint32_t c = 0;
     if (MODE != 2) {
-        c = (MODE == 1 ? cn : cf) * 2 * NW;  // this lane's 2 j-sets x 16 warps
+        c = (MODE == 1 ? cn : cf) * (NJS / 32) * SW;  // this lane's j-sets x the block's warps
     } else {
-        float tb[2][7];
+        constexpr int H = NJS / 32;  // j-sets of the block per lane
+        float tb[H][7];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < H; ++h)
 #pragma unroll
             for (int a = 0; a < 7; ++a) tb[h][a] = __ldg(p.jbox + (J * BI / JS + l + 32 * h) * 8 + a);
-        for (int w = 0; w < NW; ++w) {
+        for (int w = 0; w < SW; ++w) {
             float wb[7];
 #pragma unroll
             for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + ((I * BI + w * 128) / 128) * 8 + a);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) c += boxes_near(wb, tb[h], p.gamma) ? cn : cf;
+            for (int h = 0; h < H; ++h) c += boxes_near(wb, tb[h], p.gamma) ? cn : cf;
         }
     }
 #pragma unroll
@@ -444,12 +450,12 @@ int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint
         NB_CUDA(cudaGetLastError());
     }
     auto kern = force_sym_kernel<POL, MODE>;
-    const size_t smem = kRedBytes + 16 * NT * sizeof(Acc<POL>) +
-                        (POL == NB_PREC_F64ACC ? 16 * NT * sizeof(float) : 0);
+    const size_t smem = kRedBytes + 16 * SNT * sizeof(Acc<POL>) +
+                        (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
     static const cudaError_t optin =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NB_CUDA(optin);
-    kern<<<(unsigned)p.ctas, NT, smem, j.stream>>>(p);
+    kern<<<(unsigned)p.ctas, SNT, smem, j.stream>>>(p);
     count_launch();
     NB_CUDA(cudaGetLastError());
     const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
@@ -477,7 +483,7 @@ SymSizes sym_sizes(int64_t Np) {
     z.nb = cdiv(Np, kSymBlock);
     z.T = z.nb * (z.nb + 1) / 2;
     z.U = z.T * US;
-    z.ctas = std::min<int64_t>(device_sm_count(), z.U);
+    z.ctas = std::min<int64_t>(CPS * (int64_t)device_sm_count(), z.U);
     // Records per row: a cost-balanced range holds at least
     // (U / ctas) * (min unit cost / max unit cost) - 2 units, so a row of
     // nb * US units meets at most that many ranges plus 2; with short ranges

@@ -162,3 +162,16 @@ def test_pairs_option_and_symmetric_workspace(B):
 def test_unknown_pairs_mode_is_rejected(B):
     rc = _forces(B, opts=_opts(B, pairs=7))
     assert rc == B.NB_ERR_INVALID
+
+
+def test_batched_symmetric_workspace(B):
+    # batches (B > 1) provision the symmetric batched region unless pairs is
+    # DIRECT or the policy is FP64; it grows with N + 128 B (padded slots)
+    n, b = 100000, 64
+    sym = B.nb_workspace_bytes(n, b, _opts(B))
+    direct = B.nb_workspace_bytes(n, b, _opts(B, pairs=B.NB_PAIRS_DIRECT))
+    fp64 = B.nb_workspace_bytes(n, b, _opts(B, precision=B.NB_PREC_FP64))
+    assert sym > direct and fp64 == direct
+    slots = n + 128 * b
+    assert sym - direct >= 2 * 80 * slots  # two slot-order FP64 state buffers
+    assert B.nb_workspace_bytes(2 * n, b, _opts(B)) > sym
