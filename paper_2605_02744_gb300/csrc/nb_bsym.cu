@@ -113,9 +113,11 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
         p.pbase[p.B] = pb;
         p.rstart[blk] = (int32_t)ib;
         if (sb > p.Ns || ib > p.items_cap || pb > p.pairs_cap) {
-            dev::set_status(p.status, kStatusInvalid);  // cannot happen: bounds of bsym_layout
+            // cannot happen (bounds of bsym_layout); if it did, every system
+            // becomes empty so that no kernel indexes past the buffers
+            dev::set_status(p.status, kStatusInvalid);
             sb = ib = pb = blk = 0;
-            p.sbase[p.B] = 0;
+            for (int c = 0; c <= p.B; ++c) p.sbase[c] = p.ibase[c] = p.pbase[c] = 0;
         }
         s_tot[0] = sb;
         s_tot[1] = ib;
