@@ -124,22 +124,7 @@ __global__ void batched_setup_kernel(const int64_t *__restrict__ offsets, int B,
         keys[e] = k;
     }
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int e = tid; e < P; e += blockDim.x) {
-                const int x = e ^ j;
-                if (x > e) {
-                    const bool asc = (e & k) == 0;
-                    const unsigned long long a = keys[e], b = keys[x];
-                    if ((a > b) == asc) {
-                        keys[e] = b;
-                        keys[x] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    dev::block_bitonic_sort(keys, P);
     for (int c = tid; c < B; c += blockDim.x) order[c] = (int)(keys[c] & 0xffffffffu);
 }
 
@@ -151,14 +136,6 @@ template <int CS>
 __device__ __forceinline__ int64_t slot_lo(int64_t n, int r) {
     const int64_t a = ((n * r / CS) + kBChunk - 1) / kBChunk * kBChunk;
     return a < n ? a : n;
-}
-
-// Spreads the low 10 bits of v so that bit k lands at bit 3k.
-__device__ __forceinline__ uint32_t spread3b(uint32_t v) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) r |= ((v >> k) & 1u) << (3 * k);
-    return r;
 }
 
 // Morton order of the system's n particles (one CTA): FP64 bounding box,
@@ -208,31 +185,14 @@ __device__ void sort_system(const BatchedParams &p, int64_t o0, int n, int *perm
         if (e < n) {
             uint32_t code = 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double q = (p.pos[3 * (o0 + e) + c] - blo[c]) * scale[c];
-                q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
-                code |= spread3b((uint32_t)q) << c;
-            }
+            for (int c = 0; c < 3; ++c)
+                code |= dev::morton_part(p.pos[3 * (o0 + e) + c], blo[c], scale[c]) << c;
             k = ((unsigned long long)code << 13) | (unsigned long long)e;
         }
         keys[e] = k;
     }
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int e = tid; e < P; e += BT) {
-                const int x = e ^ j;
-                if (x > e) {
-                    const bool asc = (e & k) == 0;
-                    const unsigned long long a = keys[e], b = keys[x];
-                    if ((a > b) == asc) {
-                        keys[e] = b;
-                        keys[x] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+    dev::block_bitonic_sort(keys, P);
     for (int e = tid; e < n; e += BT) perm[e] = (int)(keys[e] & 0x1fffull);
 }
 

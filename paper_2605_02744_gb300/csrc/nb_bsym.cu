@@ -229,34 +229,13 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p, int from_use
         if (e < n) {
             uint32_t code = 0;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double q = (xsrc(e, d) - blo[d]) * scale[d];
-                q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
-                uint32_t v = (uint32_t)q, r = 0;
-#pragma unroll
-                for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
-                code |= r << d;
-            }
+            for (int d = 0; d < 3; ++d) code |= dev::morton_part(xsrc(e, d), blo[d], scale[d]) << d;
             k = ((unsigned long long)code << 13) | (unsigned long long)e;
         }
         keys[e] = k;
     }
     __syncthreads();
-    for (int k = 2; k <= P2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int e = tid; e < P2; e += blockDim.x) {
-                const int x = e ^ j;
-                if (x > e) {
-                    const bool asc = (e & k) == 0;
-                    const unsigned long long a = keys[e], b = keys[x];
-                    if ((a > b) == asc) {
-                        keys[e] = b;
-                        keys[x] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+    dev::block_bitonic_sort(keys, P2);
     for (int64_t s = tid; s < ns; s += blockDim.x) {
         double v[10];
         int pi = -1;

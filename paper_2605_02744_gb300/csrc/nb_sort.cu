@@ -74,14 +74,6 @@ __global__ void bbox_kernel(const double *__restrict__ pos, int64_t N, long long
     }
 }
 
-// Spreads the low 10 bits of v so that bit k lands at bit 3k.
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) r |= ((v >> k) & 1u) << (3 * k);
-    return r;
-}
-
 __global__ void morton_keys_kernel(const double *__restrict__ pos, int64_t N, int64_t P,
                                    const long long *__restrict__ box,
                                    unsigned long long *__restrict__ keys) {
@@ -98,11 +90,7 @@ __global__ void morton_keys_kernel(const double *__restrict__ pos, int64_t N, in
         if (i < N) {
             uint32_t code = 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double q = (pos[3 * i + c] - lo[c]) * scale[c];
-                q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
-                code |= spread3((uint32_t)q) << c;
-            }
+            for (int c = 0; c < 3; ++c) code |= dev::morton_part(pos[3 * i + c], lo[c], scale[c]) << c;
             k = ((unsigned long long)code << 32) | (unsigned long long)(uint32_t)i;
         }
         keys[i] = k;
