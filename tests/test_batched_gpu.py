@@ -191,3 +191,25 @@ def test_symmetric_and_direct_batched_paths_agree():
     assert np.abs(out["default"][0] - out["direct"][0]).max() <= 1e-5 * dx
     assert rel_vec_err(out["default"][1], out["direct"][1]).max() <= 2e-5
     assert rel_err(out["default"][2], out["direct"][2]).max() <= 2e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("f64acc", 1e-5)])
+def test_symmetric_batched_policies_and_G(prec, tol):
+    # all-FP32 totals (loose gate) and G != 1 on the symmetric batched path
+    sizes = [3000, 17, 8192, 640]
+    s = _batch(sizes, seed=4)
+    eps = _eps(len(sizes), 5)
+    G = 0.75
+    opts = binding.make_opts(prec, G=G)
+    acc = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    ws = binding.workspace(s.n, len(sizes), opts)
+    binding.nb_forces_batched(dev(s.pos), dev(s.mass), torch.tensor(s.offsets, device="cuda"),
+                              dev(eps), acc, pot, ws, opts)
+    assert binding.nb_poll_status(ws, opts) == binding.NB_OK
+    a, p = host(acc), host(pot)
+    for c in range(len(sizes)):
+        lo, hi = s.offsets[c], s.offsets[c + 1]
+        ra, rp = oracle.forces(s.pos[lo:hi], s.mass[lo:hi], eps[c], G)
+        assert rel_vec_err(a[lo:hi], ra).max() <= tol, (prec, c)
+        assert rel_err(p[lo:hi], rp).max() <= tol, (prec, c)
