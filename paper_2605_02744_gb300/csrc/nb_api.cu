@@ -401,8 +401,13 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
     NB_TRY(make_force_job(&j, s->pos, s->mass, s->N, s->eps, s->acc, s->pot, s->ws, s->ws_bytes, o));
     j.adaptive = positions_adaptive(o, s->N, nsteps > 0);
     int64_t sorted_at = -1;  // step index of the last full Morton sort
+    // the potential is evaluated only where the caller can see it: a
+    // forces-only call (nsteps = 0) or the last step of the loop
+    double *pot = s->pot;
     if (!s->acc_valid) {
-        NB_TRY(launch_force(j));
+        ForceJob f = j;
+        f.pot = nsteps == 0 ? pot : nullptr;
+        NB_TRY(launch_force(f));
         sorted_at = 0;
     }
     float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
@@ -416,6 +421,7 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
         if (j.adaptive && !k.reuse_order) sorted_at = n + 1;
         k.vel = s->vel;
         k.kick = 0.5 * dt;
+        k.pot = n == nsteps - 1 ? pot : nullptr;
         NB_TRY(launch_force(k));
     }
     return NB_OK;

@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, 
     }
 }
 
-// Persistent warps over the item queue.
-template <int POL, int MODE>
+// Persistent warps over the item queue (POT: the potential sums too).
+template <int POL, int MODE, bool POT>
 __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
     // per-warp i-side totals of the current item (FP64 policy: FP32 within
     // an item of <= 8 blocks, FP64 in the record and the fold)
@@ -423,11 +423,11 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
             const bool nqb = (near >> q) & 1u;
             float4 bs;
             if (b != a) {
-                run_set<MODE, true>(S, e2, jc, nqb, bs, -1);
+                run_set<MODE, true, POT>(S, e2, jc, nqb, bs, -1);
                 const int64_t pair = p.pbase[c] + (int64_t)b * (b - 1) / 2 + a;
                 __stcs(reinterpret_cast<float4 *>(p.P) + pair * BW + 32 * (q & 3) + l, bs);
             } else {
-                run_set<MODE, false>(S, e2, jc, nqb, bs, q & 3);
+                run_set<MODE, false, POT>(S, e2, jc, nqb, bs, q & 3);
             }
             if ((q & 3) == 3) {
 #pragma unroll
@@ -516,26 +516,37 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     constexpr int IPOL = POL == NB_PREC_F64ACC ? NB_PREC_FP32 : POL;
     const size_t item_smem = (size_t)NW * 16 * 32 * sizeof(Acc<IPOL>);
     static const cudaError_t optin_item = cudaFuncSetAttribute(
-        bsym_item_kernel<POL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)item_smem);
+        bsym_item_kernel<POL, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)item_smem);
+    static const cudaError_t optin_item_np = cudaFuncSetAttribute(
+        bsym_item_kernel<POL, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)item_smem);
     NB_CUDA(optin_item);
-    auto force = [&](double kick) {
-        bsym_item_kernel<POL, MODE><<<item_grid, NT, item_smem, st>>>(p);
+    NB_CUDA(optin_item_np);
+    // the potential is evaluated only where the caller can see it: a
+    // forces-only call, or the last step of a step loop
+    auto force = [&](double kick, bool pot) {
+        if (pot)
+            bsym_item_kernel<POL, MODE, true><<<item_grid, NT, item_smem, st>>>(p);
+        else
+            bsym_item_kernel<POL, MODE, false><<<item_grid, NT, item_smem, st>>>(p);
         bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, kick);
         count_launch(2);
     };
+    const bool want_pot = j.pot != nullptr;
     bsym_setup_kernel<<<1, 1024, 0, st>>>(p, j.N);
     count_launch();
     sort(1);
     if (!j.acc_valid || j.nsteps == 0) {
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.0, 0.0);
         count_launch();
-        force(0.0);
+        force(0.0, want_pot && j.nsteps == 0);
     }
     for (int64_t n = 0; n < j.nsteps; ++n) {
         if (n > 0 && n % kBsResort == 0) sort(0);
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.5 * j.dt, j.dt);
         count_launch();
-        force(0.5 * j.dt);
+        force(0.5 * j.dt, want_pot && n == j.nsteps - 1);
     }
     bsym_scatter_kernel<<<fold_grid, 256, 0, st>>>(p, j.nsteps > 0 ? 1 : 0);
     count_launch();

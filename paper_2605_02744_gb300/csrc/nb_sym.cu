@@ -126,8 +126,9 @@ __device__ __forceinline__ void load_j(const SymParams &p, int64_t s, float (&j)
     for (int a = 0; a < 7; ++a) j[a] = __ldg(p.soa + a * p.Np + s);
 }
 
-// MODE: 0 single-float displacement, 1 hi/lo, 2 adaptive.
-template <int POL, int MODE>
+// MODE: 0 single-float displacement, 1 hi/lo, 2 adaptive.  POT: the
+// potential sums too (the caller wants phi).
+template <int POL, int MODE, bool POT>
 __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *red = reinterpret_cast<float4 *>(smem);                   // [2][KB][SW][32]
@@ -206,10 +207,10 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
             const bool nq = (near >> q) & 1ull;
             float4 b;
             if (sym) {
-                run_set<MODE, true>(S, e2, jc, nq, b, -1);
+                run_set<MODE, true, POT>(S, e2, jc, nq, b, -1);
                 red[((half * KB + (q % KB)) * SW + w) * 32 + l] = b;
             } else {
-                run_set<MODE, false>(S, e2, jc, nq, b, (q >> 2) == w ? (q & 3) : -1);
+                run_set<MODE, false, POT>(S, e2, jc, nq, b, (q >> 2) == w ? (q & 3) : -1);
             }
             if ((q + 1) % FL == 0 || q + 1 == qb) {
 #pragma unroll
@@ -435,6 +436,20 @@ __global__ void sym_ranges_kernel(const uint32_t *cost, const unsigned long long
     }
 }
 
+template <int POL, int MODE, bool POT>
+int launch_pair(const SymParams &p, cudaStream_t st) {
+    auto kern = force_sym_kernel<POL, MODE, POT>;
+    const size_t smem = kRedBytes + 16 * SNT * sizeof(Acc<POL>) +
+                        (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
+    static const cudaError_t optin =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NB_CUDA(optin);
+    kern<<<(unsigned)p.ctas, SNT, smem, st>>>(p);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
 template <int POL, int MODE>
 int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint32_t *status) {
     {
@@ -449,15 +464,9 @@ int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint
         count_launch(3);
         NB_CUDA(cudaGetLastError());
     }
-    auto kern = force_sym_kernel<POL, MODE>;
-    const size_t smem = kRedBytes + 16 * SNT * sizeof(Acc<POL>) +
-                        (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
-    static const cudaError_t optin =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    NB_CUDA(optin);
-    kern<<<(unsigned)p.ctas, SNT, smem, j.stream>>>(p);
-    count_launch();
-    NB_CUDA(cudaGetLastError());
+    const int rc_pair = j.pot ? launch_pair<POL, MODE, true>(p, j.stream)
+                              : launch_pair<POL, MODE, false>(p, j.stream);
+    if (rc_pair != NB_OK) return rc_pair;
     const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
     sym_fold_kernel<POL><<<(unsigned)fold_blocks, 256, 0, j.stream>>>(
         p, j.N, perm, j.G, j.acc, j.pot, j.vel, j.kick, status);

@@ -46,8 +46,9 @@ struct ISet {
 
 // One rotation step: the lane's four i-slots against its current j.  With
 // SELF, i-slot self_k is the j-particle itself: its half of the pair gets a
-// zero mass (Eq. 1 leaves out j = i).
-template <bool NEAR, bool SYM, bool SELF>
+// zero mass (Eq. 1 leaves out j = i).  POT: also the potential sums (2 of
+// the 18 FP32 operations per unordered pair).
+template <bool NEAR, bool SYM, bool SELF, bool POT>
 __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float jy, float jz,
                                      float jm, float jxl, float jyl, float jzl, float &bx,
                                      float &by, float &bz, float &bp, int self_k = -1) {
@@ -73,7 +74,7 @@ __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float j
         S.ax[g] = fma2(sj, dx, S.ax[g]);
         S.ay[g] = fma2(sj, dy, S.ay[g]);
         S.az[g] = fma2(sj, dz, S.az[g]);
-        S.ph[g] = fma2(M, ri, S.ph[g]);
+        if (POT) S.ph[g] = fma2(M, ri, S.ph[g]);
         if (SYM) {
             const float2 si = mul2(S.nm[g], ri3);  // -m_i r^-3
             bx = fmaf(si.x, dx.x, bx);
@@ -82,8 +83,10 @@ __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float j
             by = fmaf(si.y, dy.y, by);
             bz = fmaf(si.x, dz.x, bz);
             bz = fmaf(si.y, dz.y, bz);
-            bp = fmaf(S.m[g].x, ri.x, bp);
-            bp = fmaf(S.m[g].y, ri.y, bp);
+            if (POT) {
+                bp = fmaf(S.m[g].x, ri.x, bp);
+                bp = fmaf(S.m[g].y, ri.y, bp);
+            }
         }
     }
 }
@@ -91,7 +94,7 @@ __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float j
 // 32 steps over one j-set; the j values (and sums) end on their home lane.
 // self_k >= 0 (diagonal items only): the j-set is the warp's own i-slots
 // 32 self_k + [0, 32), so step 0 pairs every lane with itself.
-template <bool NEAR, bool SYM>
+template <bool NEAR, bool SYM, bool POT>
 __device__ __forceinline__ void rotate_set(ISet &S, const float2 e2, const float (&j)[7],
                                            float4 &b, int self_k) {
     const int src = (threadIdx.x + 1) & 31;
@@ -111,30 +114,30 @@ __device__ __forceinline__ void rotate_set(ISet &S, const float2 e2, const float
             bx = __shfl_sync(0xffffffffu, bx, src);
             by = __shfl_sync(0xffffffffu, by, src);
             bz = __shfl_sync(0xffffffffu, bz, src);
-            bp = __shfl_sync(0xffffffffu, bp, src);
+            if (POT) bp = __shfl_sync(0xffffffffu, bp, src);
         }
     };
     int s0 = 0;
     if (self_k >= 0) {
-        step<NEAR, SYM, true>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp, self_k);
+        step<NEAR, SYM, true, POT>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp, self_k);
         rotate();
         s0 = 1;
     }
 #pragma unroll 4
     for (int s = s0; s < JS; ++s) {
-        step<NEAR, SYM, false>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp);
+        step<NEAR, SYM, false, POT>(S, e2, jx, jy, jz, jm, jxl, jyl, jzl, bx, by, bz, bp);
         rotate();
     }
     b = make_float4(bx, by, bz, bp);
 }
 
-template <int MODE, bool SYM>
+template <int MODE, bool SYM, bool POT>
 __device__ __forceinline__ void run_set(ISet &S, const float2 e2, const float (&j)[7], bool near,
                                         float4 &b, int self_k) {
     if (MODE == 1 || (MODE == 2 && near))
-        rotate_set<true, SYM>(S, e2, j, b, self_k);
+        rotate_set<true, SYM, POT>(S, e2, j, b, self_k);
     else
-        rotate_set<false, SYM>(S, e2, j, b, self_k);
+        rotate_set<false, SYM, POT>(S, e2, j, b, self_k);
 }
 
 // Adds an FP64 record value in the policy's arithmetic.
