@@ -204,9 +204,11 @@ int nb_forces_noalloc(const double *pos, const double *mass, int64_t N, double e
  * conditions are checked on the device: a violating cluster is skipped and
  * NB_ERR_INVALID is latched for nb_poll_status.  N is the total particle
  * count (the workspace is sized with nb_workspace_bytes(N, B, opts)).  FP32
- * pairs only (precision FP32, KAHAN or F64ACC; positions always split).
- * The work division over clusters follows the SPMD split of Sec. 3.1
- * (independent work per core), one system per thread-block cluster.
+ * pairs only (precision FP32, KAHAN or F64ACC).  The work division over
+ * clusters follows the SPMD split of Sec. 3.1 (independent work per core):
+ * warp-granular work items of every cluster on the symmetric path
+ * (default), one cluster per thread-block cluster on the direct path
+ * (opts->pairs = NB_PAIRS_DIRECT).
  */
 int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
                       int64_t N, const double *eps, double *acc, double *pot, void *ws,
@@ -240,9 +242,13 @@ typedef struct nb_state {
  * nsteps kick-drift-kick leapfrog steps of size dt:
  *   v += (dt/2) a(x);  x += dt v;  v += (dt/2) a(x)
  * The paper advances with a predict-evaluate-correct Hermite scheme (Sec. 2.1)
- * around the same all-pairs evaluation; this library uses leapfrog.  The
- * batched form runs every step of all clusters inside one persistent launch.
- * dt must be finite, nsteps >= 0.
+ * around the same all-pairs evaluation; this library uses leapfrog.  On
+ * return acc holds a(x) and pot (if not NULL) phi(x) at the final
+ * positions; the potential of intermediate steps is not observable and is
+ * not summed (nsteps = 0 evaluates a and phi at the current positions).
+ * The batched form runs all clusters' steps in a few launches per step
+ * (symmetric path) or one persistent launch (direct path).  dt must be
+ * finite, nsteps >= 0.
  */
 int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *opts);
 
