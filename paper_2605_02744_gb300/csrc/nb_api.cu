@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "nb_internal.h"
@@ -44,6 +46,19 @@ int device_sm_count() {
         return 152;
     }
     return n;
+}
+
+int smem_optin(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void *, int, size_t>> done;
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(kernel, dev, bytes);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return NB_OK;
+    NB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert(key);
+    return NB_OK;
 }
 
 // ------------------------------------------------------------ shapes

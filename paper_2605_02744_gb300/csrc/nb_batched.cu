@@ -543,9 +543,10 @@ static int launch_batched_cs(const BatchedParams &p, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(BT, 1, 1);
     cfg.dynamicSmemBytes = 8 * kBMaxN;  // Morton keys of one system
-    static const cudaError_t optin = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kBMaxN));
-    (void)optin;
+    {
+        const int rc = smem_optin(reinterpret_cast<const void *>(kern), 8 * (size_t)kBMaxN);
+        if (rc != NB_OK) return rc;
+    }
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -622,11 +623,9 @@ int launch_batched(const BatchedJob &j) {
         int P = 1;
         while (P < j.B && P < kBSortMax) P <<= 1;
         const size_t smem = j.B <= kBSortMax ? (size_t)P * 8 : 0;
-        static std::once_flag once;
-        std::call_once(once, [] {
-            cudaFuncSetAttribute(batched_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kBSortMax * 8);
-        });
+        const int rc = smem_optin(reinterpret_cast<const void *>(batched_setup_kernel),
+                                  (size_t)kBSortMax * 8);
+        if (rc != NB_OK) return rc;
         batched_setup_kernel<<<1, 1024, smem, j.stream>>>(j.offsets, j.B, j.N, j.eps,
                                                           const_cast<int *>(p.order), p.counter,
                                                           p.status);

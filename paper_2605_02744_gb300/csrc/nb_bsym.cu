@@ -504,9 +504,10 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     const unsigned fold_grid = (unsigned)std::min<int64_t>(cdiv(nb_max * BW, 256), 64 * (int64_t)device_sm_count());
     const unsigned item_grid = (unsigned)device_sm_count();
     constexpr int sort_smem = 12 * kBsMaxN;  // keys and the old permutation
-    static const cudaError_t optin = cudaFuncSetAttribute(
-        bsym_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
-    NB_CUDA(optin);
+    {
+        const int rc = smem_optin(reinterpret_cast<const void *>(bsym_sort_kernel), sort_smem);
+        if (rc != NB_OK) return rc;
+    }
     p.cur = 0;
     auto sort = [&](int from_user) {
         bsym_sort_kernel<<<(unsigned)p.B, 512, sort_smem, st>>>(p, from_user);
@@ -515,14 +516,11 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     };
     constexpr int IPOL = POL == NB_PREC_F64ACC ? NB_PREC_FP32 : POL;
     const size_t item_smem = (size_t)NW * 16 * 32 * sizeof(Acc<IPOL>);
-    static const cudaError_t optin_item = cudaFuncSetAttribute(
-        bsym_item_kernel<POL, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)item_smem);
-    static const cudaError_t optin_item_np = cudaFuncSetAttribute(
-        bsym_item_kernel<POL, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)item_smem);
-    NB_CUDA(optin_item);
-    NB_CUDA(optin_item_np);
+    for (const void *k : {reinterpret_cast<const void *>(bsym_item_kernel<POL, MODE, true>),
+                          reinterpret_cast<const void *>(bsym_item_kernel<POL, MODE, false>)}) {
+        const int rc = smem_optin(k, item_smem);
+        if (rc != NB_OK) return rc;
+    }
     // the potential is evaluated only where the caller can see it: a
     // forces-only call, or the last step of a step loop
     auto force = [&](double kick, bool pot) {

@@ -418,10 +418,10 @@ static int launch_sk(const ForceParams &p, int cps, cudaStream_t st) {
     auto kern = force_sk_kernel<NT, IR, TJ, ST, POL, GUARD, SPLIT, NF>;
     const size_t smem = (size_t)ST * (SPLIT ? 7 : 4) * 4 * TJ + (size_t)ST * 8;
     // stages above 48 KB need the opt-in (up to 227 KB per CTA)
-    static const int optin = smem > 48 * 1024
-        ? (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-        : 0;
-    (void)optin;
+    if (smem > 48 * 1024) {
+        const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
+        if (rc != NB_OK) return rc;
+    }
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);

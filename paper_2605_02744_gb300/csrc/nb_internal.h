@@ -46,6 +46,10 @@ bool shape_compiled(const Shape &s, int kind);
 enum Kind { kKindForce = 0, kKindVjp = 1 };
 
 int device_sm_count();
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per kernel, device and size (thread-safe); a failure is
+// returned as NB_ERR_CUDA.
+int smem_optin(const void *kernel, size_t bytes);
 // Counts kernels this library enqueued (nb_launch_count); a CUDA-graph
 // replay launches the captured kernels without passing through here.
 void count_launch(int n = 1);

@@ -441,9 +441,8 @@ int launch_pair(const SymParams &p, cudaStream_t st) {
     auto kern = force_sym_kernel<POL, MODE, POT>;
     const size_t smem = kRedBytes + 16 * SNT * sizeof(Acc<POL>) +
                         (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
-    static const cudaError_t optin =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    NB_CUDA(optin);
+    const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
+    if (rc != NB_OK) return rc;
     kern<<<(unsigned)p.ctas, SNT, smem, st>>>(p);
     count_launch();
     NB_CUDA(cudaGetLastError());
