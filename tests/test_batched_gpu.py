@@ -213,3 +213,24 @@ def test_symmetric_batched_policies_and_G(prec, tol):
         ra, rp = oracle.forces(s.pos[lo:hi], s.mass[lo:hi], eps[c], G)
         assert rel_vec_err(a[lo:hi], ra).max() <= tol, (prec, c)
         assert rel_err(p[lo:hi], rp).max() <= tol, (prec, c)
+
+
+def test_symmetric_batched_thousands_of_tiny_clusters():
+    # 3000 clusters of 1..40 particles: one 128-slot block each, the setup's
+    # prefix sums and item order over many systems
+    sizes = np.random.default_rng(12).integers(1, 41, 3000)
+    s = _batch(list(sizes), seed=13)
+    eps = _eps(len(sizes), 7)
+    opts = binding.make_opts("kahan")
+    acc = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    ws = binding.workspace(s.n, len(sizes), opts)
+    binding.nb_forces_batched(dev(s.pos), dev(s.mass), torch.tensor(s.offsets, device="cuda"),
+                              dev(eps), acc, pot, ws, opts)
+    assert binding.nb_poll_status(ws, opts) == binding.NB_OK
+    a, p = host(acc), host(pot)
+    for c in list(range(0, 3000, 97)) + [2999]:
+        lo, hi = s.offsets[c], s.offsets[c + 1]
+        ra, rp = oracle.forces(s.pos[lo:hi], s.mass[lo:hi], eps[c])
+        assert rel_vec_err(a[lo:hi], ra).max() <= 1e-5, c
+        assert rel_err(p[lo:hi], rp).max() <= 1e-5, c

@@ -125,3 +125,24 @@ def test_refusals():
     a, p = _forces(s, 0.0, "f64acc", pairs="default")
     ra, rp = oracle.forces(s.pos, s.mass, 0.0)
     assert rel_vec_err(a, ra).max() <= 1e-5
+
+
+def test_top_of_default_range_sampled_rows():
+    # 2^21 - 12345 particles: 1024 row blocks with a ragged last one, the
+    # largest default symmetric evaluation (17 GB of j-side partials)
+    n = (1 << 21) - 12345
+    s = ics.plummer(n, seed=21)
+    r = np.linalg.norm(s.pos, axis=1)
+    order = np.argsort(r)
+    rows = np.unique(np.concatenate([np.random.default_rng(8).choice(n, 400, replace=False),
+                                     order[:32], order[-32:], np.arange(n - 40, n)]))
+    o = binding.make_opts("kahan")
+    acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = binding.workspace(n, 1, o)
+    binding.nb_forces(dev(s.pos), dev(s.mass), 1e-3, acc, pot, ws, o)
+    assert binding.nb_poll_status(ws, o) == binding.NB_OK
+    ra, rp = oracle.forces_rows(s.pos, s.mass, 1e-3, rows)
+    assert rel_vec_err(host(acc)[rows], ra).max() <= 1e-5
+    assert rel_err(host(pot)[rows], rp).max() <= 1e-5
+    del ws
