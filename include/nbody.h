@@ -93,7 +93,8 @@ typedef enum {
  * needs eps > 0 and a workspace of about N^2 / 256 bytes for the j-side
  * partial sums (4.3 GB at N = 2^20), which nb_workspace_bytes includes when
  * the path is in use.  DEFAULT takes SYMMETRIC for 32768 <= N <= 2^21 and
- * eps > 0, DIRECT otherwise.  For batches (B > 1, nb_forces_batched and
+ * eps > 0, DIRECT otherwise; FP64 pairs (NB_PREC_FP64) keep FP64 partials,
+ * twice the bytes, and DEFAULT takes them for 32768 <= N <= 2^20.  For batches (B > 1, nb_forces_batched and
  * nb_step with offsets) DEFAULT and SYMMETRIC take the symmetric batched
  * path (warp-granular work items; workspace about 250 B per particle plus
  * 2 KiB per pair of 128-particle blocks of a cluster: 0.9 GB for 512

@@ -472,6 +472,10 @@ int launch_force(const ForceJob &j) {
     const bool guard = (j.eps == 0.0);
     uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     if (j.precision == NB_PREC_FP64) {
+        if (j.sym) {
+            if (guard) return fail(NB_ERR_UNSUPPORTED, "symmetric pairs need eps > 0");
+            return launch_force_sym(j, false);
+        }
         constexpr int NT = 128;
         const int64_t grid = cdiv(j.N, NT);
         count_launch();

@@ -101,6 +101,11 @@ struct SymParams {
     double *rec;        // [nb][K][BI][4]
     const int64_t *lo;  // [ctas + 1]: CTA c owns units [lo[c], lo[c + 1])
     uint32_t *status;
+    // FP64 pairs: positions [N][3] and masses in particle order, FP64 partials
+    const double *pos64, *mass64;
+    int64_t N;
+    double eps2_64;
+    double *P64;        // [nb (nb - 1) / 2][BI][4]
 };
 
 __host__ __device__ inline int64_t row_start(int64_t I, int64_t nb) {
@@ -327,6 +332,221 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
     if (bad) dev::set_status(status, kStatusNonFinite);
 }
 
+// ------------------------------------------------------------- FP64 pairs
+// The same decomposition with FP64 arithmetic throughout (positions, pairs,
+// sums), for the FP64 policy: each unordered pair once, its j-side sums
+// rotated through the lanes as doubles.  The slots are the particles in
+// their own order (no packing, no near/far choice); one rsqrt per unordered
+// pair instead of two.
+struct alignas(16) D4 {
+    double x, y, z, w;
+};
+
+struct ISet64 {
+    double x[IR], y[IR], z[IR], m[IR];
+    double ax[IR], ay[IR], az[IR], ph[IR];
+};
+
+template <bool SYM, bool SELF, bool POT>
+__device__ __forceinline__ void step64(ISet64 &S, double eps2, double jx, double jy, double jz,
+                                       double jm, double &bx, double &by, double &bz, double &bp,
+                                       int self_k) {
+#pragma unroll
+    for (int k = 0; k < IR; ++k) {
+        const double mj = (SELF && k == self_k) ? 0.0 : jm;
+        const double dx = jx - S.x[k], dy = jy - S.y[k], dz = jz - S.z[k];
+        const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+        const double ri = rsqrt(r2);
+        const double ri3 = ri * ri * ri;
+        const double sj = mj * ri3;
+        S.ax[k] = fma(sj, dx, S.ax[k]);
+        S.ay[k] = fma(sj, dy, S.ay[k]);
+        S.az[k] = fma(sj, dz, S.az[k]);
+        if (POT) S.ph[k] = fma(mj, ri, S.ph[k]);
+        if (SYM) {
+            const double si = S.m[k] * ri3;
+            bx = fma(-si, dx, bx);
+            by = fma(-si, dy, by);
+            bz = fma(-si, dz, bz);
+            if (POT) bp = fma(S.m[k], ri, bp);
+        }
+    }
+}
+
+template <bool SYM, bool POT>
+__device__ __forceinline__ void rotate_set64(ISet64 &S, double eps2, const double (&j)[4],
+                                             D4 &b, int self_k) {
+    const int src = (threadIdx.x + 1) & 31;
+    double jx = j[0], jy = j[1], jz = j[2], jm = j[3];
+    double bx = 0.0, by = 0.0, bz = 0.0, bp = 0.0;
+    auto rotate = [&]() {
+        jx = __shfl_sync(0xffffffffu, jx, src);
+        jy = __shfl_sync(0xffffffffu, jy, src);
+        jz = __shfl_sync(0xffffffffu, jz, src);
+        jm = __shfl_sync(0xffffffffu, jm, src);
+        if (SYM) {
+            bx = __shfl_sync(0xffffffffu, bx, src);
+            by = __shfl_sync(0xffffffffu, by, src);
+            bz = __shfl_sync(0xffffffffu, bz, src);
+            if (POT) bp = __shfl_sync(0xffffffffu, bp, src);
+        }
+    };
+    int s0 = 0;
+    if (self_k >= 0) {
+        step64<SYM, true, POT>(S, eps2, jx, jy, jz, jm, bx, by, bz, bp, self_k);
+        rotate();
+        s0 = 1;
+    }
+#pragma unroll 2
+    for (int st = s0; st < JS; ++st) {
+        step64<SYM, false, POT>(S, eps2, jx, jy, jz, jm, bx, by, bz, bp, -1);
+        rotate();
+    }
+    b = D4{bx, by, bz, bp};
+}
+
+__device__ __forceinline__ void load_j64(const SymParams &p, int64_t s, double (&j)[4]) {
+    if (s < p.N) {
+        j[0] = __ldg(p.pos64 + 3 * s);
+        j[1] = __ldg(p.pos64 + 3 * s + 1);
+        j[2] = __ldg(p.pos64 + 3 * s + 2);
+        j[3] = __ldg(p.mass64 + s);
+    } else {
+        j[0] = j[1] = j[2] = j[3] = 0.0;  // padding: zero mass at the origin
+    }
+}
+
+constexpr size_t kRed64Bytes = 2 * KB * SW * 32 * sizeof(D4);
+
+template <bool POT>
+__global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams p) {
+    extern __shared__ __align__(16) unsigned char smem64[];
+    D4 *red = reinterpret_cast<D4 *>(smem64);  // [2][KB][SW][32]
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    const int64_t c = blockIdx.x;
+    int64_t u = __ldg(p.lo + c);
+    const int64_t u_end = __ldg(p.lo + c + 1);
+    if (u >= u_end) return;
+    const int64_t t0 = u / US;
+    int64_t I = 0;
+    while (row_start(I + 1, p.nb) <= t0) ++I;
+    int64_t J = I + (t0 - row_start(I, p.nb));
+    ISet64 S;
+    int half = 0;
+    bool row_open = false;
+    while (u < u_end) {
+        const int qa = (int)(u % US) * KB;
+        const int64_t item_end = (u / US + 1) * US;
+        const int64_t seg_end = item_end < u_end ? item_end : u_end;
+        const int qb = qa + (int)(seg_end - u) * KB;
+        const int64_t ib = I * BI + w * 128;
+        if (!row_open) {
+#pragma unroll
+            for (int k = 0; k < IR; ++k) {
+                double v[4];
+                load_j64(p, ib + 32 * k + l, v);
+                S.x[k] = v[0];
+                S.y[k] = v[1];
+                S.z[k] = v[2];
+                S.m[k] = v[3];
+                S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = 0.0;
+            }
+            row_open = true;
+        }
+        const bool sym = J != I;
+        const int64_t jb = J * BI;
+        const int64_t pidx = J * (J - 1) / 2 + I;
+        double jn[4];
+        load_j64(p, jb + qa * JS + l, jn);
+        for (int q = qa; q < qb; ++q) {
+            double jc[4] = {jn[0], jn[1], jn[2], jn[3]};
+            if (q + 1 < qb) load_j64(p, jb + (q + 1) * JS + l, jn);
+            D4 b;
+            if (sym) {
+                rotate_set64<true, POT>(S, p.eps2_64, jc, b, -1);
+                red[((half * KB + (q % KB)) * SW + w) * 32 + l] = b;
+            } else {
+                rotate_set64<false, POT>(S, p.eps2_64, jc, b, (q >> 2) == w ? (q & 3) : -1);
+            }
+            if (sym && (q + 1) % KB == 0) {
+                __syncthreads();
+                for (int v = tid; v < KB * JS * 4; v += SNT) {
+                    const int qq = v >> 7, ll = (v >> 2) & 31, e = v & 3;
+                    const double *r = reinterpret_cast<const double *>(red) +
+                                      ((half * KB + qq) * SW * 32 + ll) * 4 + e;
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w2 = 0; w2 < SW; ++w2) sum += r[w2 * 32 * 4];
+                    __stcs(p.P64 + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, sum);
+                }
+                half ^= 1;
+            }
+        }
+        u = seg_end;
+        if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
+            const int64_t k = c - range_owner(p.lo, p.ctas, row_start(I, p.nb) * US);
+            if (k >= p.K && tid == 0) dev::set_status(p.status, kStatusInvalid);
+#pragma unroll
+            for (int kk = 0; kk < IR; ++kk) {
+                if (k >= p.K) break;
+                double *r = p.rec + (((I * p.K + k) * BI) + w * 128 + 32 * kk + l) * 4;
+                __stcs(reinterpret_cast<double2 *>(r), make_double2(S.ax[kk], S.ay[kk]));
+                __stcs(reinterpret_cast<double2 *>(r) + 1, make_double2(S.az[kk], S.ph[kk]));
+            }
+            row_open = false;
+        }
+        if (qb == NJS && ++J == p.nb) {
+            ++I;
+            J = I;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) sym_fold64_kernel(const SymParams p, double G,
+                                                         double *__restrict__ acc,
+                                                         double *__restrict__ pot,
+                                                         double *__restrict__ vel, double kick,
+                                                         uint32_t *status) {
+    uint32_t bad = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = s / BI, r = s % BI;
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        const int64_t rs = row_start(I, p.nb);
+        const int64_t c0 = range_owner(p.lo, p.ctas, rs * US);
+        const int64_t c1 = range_owner(p.lo, p.ctas, (rs + (p.nb - I)) * US - 1);
+        for (int64_t k = 0; k <= c1 - c0 && k < p.K; ++k) {
+            if (__ldg(p.lo + c0 + k) == __ldg(p.lo + c0 + k + 1)) continue;  // empty range
+            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + (((I * p.K + k) * BI) + r) * 4);
+            const double2 u = __ldg(rr), v = __ldg(rr + 1);
+            a[0] += u.x;
+            a[1] += u.y;
+            a[2] += v.x;
+            a[3] += v.y;
+        }
+        const D4 *P4 = reinterpret_cast<const D4 *>(p.P64) + (I * (I - 1) / 2) * BI + r;
+        for (int64_t i2 = 0; i2 < I; ++i2) {
+            const D4 v = P4[i2 * BI];
+            a[0] += v.x;
+            a[1] += v.y;
+            a[2] += v.z;
+            a[3] += v.w;
+        }
+        const double ax = G * a[0], ay = G * a[1], az = G * a[2], gp = -G * a[3];
+        acc[3 * s] = ax;
+        acc[3 * s + 1] = ay;
+        acc[3 * s + 2] = az;
+        if (vel) {
+            vel[3 * s] += kick * ax;
+            vel[3 * s + 1] += kick * ay;
+            vel[3 * s + 2] += kick * az;
+        }
+        if (pot) pot[s] = gp;
+        if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
+    }
+    if (bad) dev::set_status(status, kStatusNonFinite);
+}
+
 // ------------------------------------------------ cost-weighted stream-K
 // Relative cost of one (warp, j-set) of an item.  Far pairs: the FP32 pipe
 // cycles per lane and step (off-diagonal 18, diagonal i-side only 13).  Near
@@ -474,6 +694,38 @@ int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint
     return NB_OK;
 }
 
+template <bool POT>
+int launch_pair64(const SymParams &p, cudaStream_t st) {
+    auto kern = force_sym64_kernel<POT>;
+    const int rc = smem_optin(reinterpret_cast<const void *>(kern), kRed64Bytes);
+    if (rc != NB_OK) return rc;
+    kern<<<(unsigned)p.ctas, SNT, kRed64Bytes, st>>>(p);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+int launch_sym64(const SymParams &p, const ForceJob &j, uint32_t *status) {
+    uint32_t *cost = reinterpret_cast<uint32_t *>(j.ws + j.L.sym_cost);
+    unsigned long long *prefix = reinterpret_cast<unsigned long long *>(
+        j.ws + j.L.sym_cost + align_up(4 * (size_t)p.T, 256));
+    int64_t *lo = const_cast<int64_t *>(p.lo);
+    sym_cost_kernel<0><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, cost);
+    sym_scan_kernel<<<1, 1024, 0, j.stream>>>(cost, p.T, prefix);
+    sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(cost, prefix, p.T,
+                                                                             p.ctas, lo);
+    count_launch(3);
+    NB_CUDA(cudaGetLastError());
+    const int rc = j.pot ? launch_pair64<true>(p, j.stream) : launch_pair64<false>(p, j.stream);
+    if (rc != NB_OK) return rc;
+    const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
+    sym_fold64_kernel<<<(unsigned)fold_blocks, 256, 0, j.stream>>>(p, j.G, j.acc, j.pot, j.vel,
+                                                                   j.kick, status);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
 template <int POL>
 int launch_sym_pol(const SymParams &p, const ForceJob &j, int mode, const int *perm,
                    uint32_t *status) {
@@ -536,12 +788,18 @@ int launch_force_sym(const ForceJob &j, bool adaptive) {
     uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     p.status = status;
     const int mode = adaptive ? 2 : (j.split ? 1 : 0);
+    p.pos64 = j.pos;
+    p.mass64 = j.mass;
+    p.N = j.N;
+    p.eps2_64 = j.eps * j.eps;
+    p.P64 = reinterpret_cast<double *>(j.ws + j.L.sym_p);
     switch (j.precision) {
+        case NB_PREC_FP64: return launch_sym64(p, j, status);
         case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, mode, perm, status);
         case NB_PREC_KAHAN: return launch_sym_pol<NB_PREC_KAHAN>(p, j, mode, perm, status);
         case NB_PREC_F64ACC: return launch_sym_pol<NB_PREC_F64ACC>(p, j, mode, perm, status);
     }
-    return fail(NB_ERR_UNSUPPORTED, "symmetric pairs compute FP32 pairs (FP32, KAHAN, F64ACC)");
+    return fail(NB_ERR_INVALID, "unknown precision %d", j.precision);
 }
 
 }  // namespace nb

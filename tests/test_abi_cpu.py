@@ -154,8 +154,15 @@ def test_pairs_option_and_symmetric_workspace(B):
     small_default = B.nb_workspace_bytes(1000, 1, o)
     small_sym = B.nb_workspace_bytes(1000, 1, _opts(B, pairs=B.NB_PAIRS_SYMMETRIC))
     assert small_sym > small_default
-    # FP64 pairs and batched systems never take it
-    assert B.nb_workspace_bytes(n, 1, _opts(B, precision=B.NB_PREC_FP64)) < default
+    # FP64 pairs keep FP64 partials (twice the bytes) and leave the default
+    # range above 2^20; batches take the batched path instead
+    fp64 = _opts(B, precision=B.NB_PREC_FP64)
+    fp64_direct = _opts(B, precision=B.NB_PREC_FP64, pairs=B.NB_PAIRS_DIRECT)
+    assert (B.nb_workspace_bytes(n, 1, fp64) - B.nb_workspace_bytes(n, 1, fp64_direct)
+            >= 2 * partials)
+    above = n + 2048
+    assert (B.nb_workspace_bytes(above, 1, fp64)
+            == B.nb_workspace_bytes(above, 1, fp64_direct))
     assert B.nb_workspace_bytes(n, 4, o) < default
 
 

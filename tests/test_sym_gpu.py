@@ -146,3 +146,29 @@ def test_top_of_default_range_sampled_rows():
     assert rel_vec_err(host(acc)[rows], ra).max() <= 1e-5
     assert rel_err(host(pot)[rows], rp).max() <= 1e-5
     del ws
+
+
+@pytest.mark.parametrize("n", [1, 2, 100, 2049, 5000, 34000])
+def test_symmetric_fp64_matches_oracle(n):
+    # FP64 pairs and sums with each unordered pair once: the FP64 gate
+    s = _system(n, n + 1)
+    eps = 0.01 if n < 30000 else 2e-3
+    ra, rp = oracle.forces(s.pos, s.mass, eps)
+    a, p = _forces(s, eps, "fp64")
+    assert rel_vec_err(a, ra).max() <= 1e-12 and rel_err(p, rp).max() <= 1e-12
+    d, dp = _forces(s, eps, "fp64", pairs="direct")
+    assert rel_vec_err(a, d).max() <= 1e-12
+
+
+def test_symmetric_fp64_step_loop():
+    s = ics.plummer_lognormal(40000, seed=17)
+    eps, h, steps = 1e-3, 1e-4, 5
+    g = api.System(s.pos, s.vel, s.mass, eps, precision="fp64")  # default: symmetric
+    b = api.System(s.pos, s.vel, s.mass, eps, precision="fp64", pairs="direct")
+    g.step(h, steps)
+    b.step(h, steps)
+    assert g.poll() == binding.NB_OK
+    dx = np.abs(host(b.pos) - s.pos).max()
+    assert np.abs(host(g.pos) - host(b.pos)).max() <= 1e-12 * max(dx, 1.0)
+    assert rel_vec_err(host(g.acc), host(b.acc)).max() <= 1e-12
+    assert rel_err(host(g.pot), host(b.pot)).max() <= 1e-12
