@@ -101,7 +101,11 @@ struct SymParams {
     double *rec;        // [nb][K][BI][4]
     const int64_t *lo;  // [ctas + 1]: CTA c owns units [lo[c], lo[c + 1])
     uint32_t *status;
-    // FP64 pairs: positions [N][3] and masses in particle order, FP64 partials
+};
+
+// FP64 pairs: the common layout plus positions [N][3] and masses in
+// particle order and FP64 partials.
+struct SymParams64 : SymParams {
     const double *pos64, *mass64;
     int64_t N;
     double eps2_64;
@@ -405,7 +409,7 @@ __device__ __forceinline__ void rotate_set64(ISet64 &S, double eps2, const doubl
     b = D4{bx, by, bz, bp};
 }
 
-__device__ __forceinline__ void load_j64(const SymParams &p, int64_t s, double (&j)[4]) {
+__device__ __forceinline__ void load_j64(const SymParams64 &p, int64_t s, double (&j)[4]) {
     if (s < p.N) {
         j[0] = __ldg(p.pos64 + 3 * s);
         j[1] = __ldg(p.pos64 + 3 * s + 1);
@@ -419,7 +423,7 @@ __device__ __forceinline__ void load_j64(const SymParams &p, int64_t s, double (
 constexpr size_t kRed64Bytes = 2 * KB * SW * 32 * sizeof(D4);
 
 template <bool POT>
-__global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams p) {
+__global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64 p) {
     extern __shared__ __align__(16) unsigned char smem64[];
     D4 *red = reinterpret_cast<D4 *>(smem64);  // [2][KB][SW][32]
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams p
     }
 }
 
-__global__ void __launch_bounds__(256) sym_fold64_kernel(const SymParams p, double G,
+__global__ void __launch_bounds__(256) sym_fold64_kernel(const SymParams64 p, double G,
                                                          double *__restrict__ acc,
                                                          double *__restrict__ pot,
                                                          double *__restrict__ vel, double kick,
@@ -695,7 +699,7 @@ int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint
 }
 
 template <bool POT>
-int launch_pair64(const SymParams &p, cudaStream_t st) {
+int launch_pair64(const SymParams64 &p, cudaStream_t st) {
     auto kern = force_sym64_kernel<POT>;
     const int rc = smem_optin(reinterpret_cast<const void *>(kern), kRed64Bytes);
     if (rc != NB_OK) return rc;
@@ -705,7 +709,7 @@ int launch_pair64(const SymParams &p, cudaStream_t st) {
     return NB_OK;
 }
 
-int launch_sym64(const SymParams &p, const ForceJob &j, uint32_t *status) {
+int launch_sym64(const SymParams64 &p, const ForceJob &j, uint32_t *status) {
     uint32_t *cost = reinterpret_cast<uint32_t *>(j.ws + j.L.sym_cost);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(
         j.ws + j.L.sym_cost + align_up(4 * (size_t)p.T, 256));
@@ -788,13 +792,17 @@ int launch_force_sym(const ForceJob &j, bool adaptive) {
     uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     p.status = status;
     const int mode = adaptive ? 2 : (j.split ? 1 : 0);
-    p.pos64 = j.pos;
-    p.mass64 = j.mass;
-    p.N = j.N;
-    p.eps2_64 = j.eps * j.eps;
-    p.P64 = reinterpret_cast<double *>(j.ws + j.L.sym_p);
+    if (j.precision == NB_PREC_FP64) {
+        SymParams64 p64;
+        static_cast<SymParams &>(p64) = p;
+        p64.pos64 = j.pos;
+        p64.mass64 = j.mass;
+        p64.N = j.N;
+        p64.eps2_64 = j.eps * j.eps;
+        p64.P64 = reinterpret_cast<double *>(j.ws + j.L.sym_p);
+        return launch_sym64(p64, j, status);
+    }
     switch (j.precision) {
-        case NB_PREC_FP64: return launch_sym64(p, j, status);
         case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, mode, perm, status);
         case NB_PREC_KAHAN: return launch_sym_pol<NB_PREC_KAHAN>(p, j, mode, perm, status);
         case NB_PREC_F64ACC: return launch_sym_pol<NB_PREC_F64ACC>(p, j, mode, perm, status);
