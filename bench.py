@@ -3,7 +3,7 @@
 
 Metric: G pair-interactions/s on a 2^20-particle Plummer sphere (eps = 1e-3,
 FP32 pairs with Kahan-compensated accumulation), one step = one kick-drift-kick
-leapfrog step through nb_step (kick + drift, Morton-sorted FP32 pack, the
+leapfrog step through nb_step (kick + drift, Hilbert-sorted FP32 pack, the
 all-pairs force + potential evaluation, its fold with the closing half-kick)
 followed by nb_energy.  Interactions are counted as N^2 per step, the
 metric's convention; the default symmetric-pair path evaluates each
@@ -269,7 +269,7 @@ def batched_rate(torch, steps=1000):
     inter = float((sizes ** 2).sum()) * steps
     return {"workload": f"512 Plummer clusters, N_c log-uniform [64, 8192] (seed 1), "
                         f"eps=0.01, {steps} KDK steps dt=1e-3, F64ACC, symmetric pairs "
-                        f"(warp-granular items, per-cluster Morton order), one CUDA graph",
+                        f"(warp-granular items, per-cluster Hilbert order), one CUDA graph",
             "ms": ms, "value": inter / (ms * 1e-3) / 1e9, "unit": UNIT, "status": ok,
             "interactions": inter}
 

@@ -78,7 +78,7 @@ typedef enum {
                            from there; FP32: SINGLE                        */
     NB_POS_SPLIT = 1,
     NB_POS_SINGLE = 2,
-    NB_POS_ADAPTIVE = 3 /* particles sorted along a Morton curve each call;
+    NB_POS_ADAPTIVE = 3 /* particles sorted along a Hilbert curve each call;
                            SPLIT for tile pairs whose bounding boxes are
                            closer than near_gamma (default 1/64) times
                            their largest coordinate, SINGLE for the rest   */

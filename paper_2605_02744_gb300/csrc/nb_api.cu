@@ -190,7 +190,7 @@ bool positions_split(const nb_opts *o) {
 }
 
 // Default thresholds of the adaptive path: a single evaluation pays a full
-// Morton sort, a step loop sorts once per kResortEvery steps.
+// Hilbert sort, a step loop sorts once per kResortEvery steps.
 constexpr int64_t kAdaptiveMinN = 1 << 18;
 constexpr int64_t kAdaptiveMinNStepping = 1 << 15;
 
@@ -419,7 +419,7 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
     ForceJob j;
     NB_TRY(make_force_job(&j, s->pos, s->mass, s->N, s->eps, s->acc, s->pot, s->ws, s->ws_bytes, o));
     j.adaptive = positions_adaptive(o, s->N, nsteps > 0);
-    int64_t sorted_at = -1;  // step index of the last full Morton sort
+    int64_t sorted_at = -1;  // step index of the last full Hilbert sort
     // the potential is evaluated only where the caller can see it: a
     // forces-only call (nsteps = 0) or the last step of the loop
     double *pot = s->pot;
@@ -431,7 +431,7 @@ static int step_single_direct(nb_state *s, double dt, int64_t nsteps, const nb_o
     }
     float *soa = reinterpret_cast<float *>(j.ws + j.L.packA);
     for (int64_t n = 0; n < nsteps; ++n) {
-        // the adaptive path packs in Morton order inside launch_force
+        // the adaptive path packs in Hilbert order inside launch_force
         NB_TRY(launch_kick_drift_pack(s->pos, s->vel, s->acc, s->mass, s->N, j.L.Np, dt,
                                       j.adaptive ? nullptr : soa, j.stream));
         ForceJob k = j;

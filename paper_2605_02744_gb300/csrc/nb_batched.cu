@@ -9,7 +9,7 @@
 // bitonic sort of the sizes) and runs every leapfrog step of that system
 // before taking the next.
 //
-// A system's particles are visited in Morton order: CTA 0 sorts them (FP64
+// A system's particles are visited in Hilbert order: CTA 0 sorts them (FP64
 // bounding box, 30-bit codes, shared-memory bitonic sort) when the system
 // starts and every 16 steps; slot s of the order holds particle perm[s], and
 // CTA r owns a 64-aligned range of slots.
@@ -25,7 +25,7 @@
 // CTAs of the cluster wrote them) into shared memory, the next tile
 // prefetched into registers during the current one.  Each thread keeps 2
 // consecutive slots in registers, so a warp's i-particles are a compact run
-// of the Morton curve; per j-chunk of 64 slots a warp takes the single-float
+// of the Hilbert curve; per j-chunk of 64 slots a warp takes the single-float
 // displacement when the chunk's box is at least gamma * max|x| away from the
 // warp's box (rounding error of x_j - x_i at most 2^-24 max|x| per
 // coordinate, so relative error <= 2^-24 / gamma), else the hi/lo one.  When
@@ -38,6 +38,7 @@
 #include <mutex>
 
 #include "nb_device.cuh"
+#include "nb_order.cuh"
 #include "nb_internal.h"
 
 namespace cg = cooperative_groups;
@@ -55,7 +56,7 @@ constexpr int kBMaxSlots = 4096;
 
 constexpr int kBMaxClusters = 320;  // resident thread-block clusters served
 constexpr int kBChunk = 64;         // slots per box
-constexpr int kBResort = 16;        // steps between Morton re-sorts of a system
+constexpr int kBResort = 16;        // steps between Hilbert re-sorts of a system
 constexpr size_t kBPermBytes = 4 * (size_t)kBMaxClusters * kBMaxN;
 constexpr size_t kBBoxBytes = 4 * (size_t)kBMaxClusters * 2 * (kBMaxN / kBChunk) * 8;
 
@@ -84,7 +85,7 @@ struct BatchedParams {
     unsigned *counter;
     int *slots;
     uint32_t *status;
-    // Morton order per thread-block cluster (adaptive displacement)
+    // Hilbert order per thread-block cluster (adaptive displacement)
     int *perm;          // [clusters][kBMaxN]: sorted slot -> local particle index
     float *boxes;       // [clusters][2][kBMaxN / 64][8]: per 64-slot chunk boxes
     float gamma;        // far iff box gap >= gamma * max|x|; < 0: split everywhere
@@ -129,7 +130,7 @@ __global__ void batched_setup_kernel(const int64_t *__restrict__ offsets, int B,
 }
 
 // ---------------------------------------------------------------- pieces
-// Slots of a system are its particles in Morton order; CTA r of the cluster
+// Slots of a system are its particles in Hilbert order; CTA r of the cluster
 // owns the 64-aligned slot range [slot_lo(r), slot_lo(r+1)), so every box
 // chunk of 64 slots has exactly one owner.
 template <int CS>
@@ -138,7 +139,7 @@ __device__ __forceinline__ int64_t slot_lo(int64_t n, int r) {
     return a < n ? a : n;
 }
 
-// Morton order of the system's n particles (one CTA): FP64 bounding box,
+// Hilbert order of the system's n particles (one CTA): FP64 bounding box,
 // 30-bit codes, keys code << 13 | local index (unique), shared-memory
 // bitonic sort, perm[slot] = local index.
 template <int BT>
@@ -183,10 +184,9 @@ __device__ void sort_system(const BatchedParams &p, int64_t o0, int n, int *perm
     for (int e = tid; e < P; e += BT) {
         unsigned long long k = ~0ull;
         if (e < n) {
-            uint32_t code = 0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                code |= dev::morton_part(p.pos[3 * (o0 + e) + c], blo[c], scale[c]) << c;
+            const uint32_t code = dev::hilbert30(dev::cell10(p.pos[3 * (o0 + e)], blo[0], scale[0]),
+                                  dev::cell10(p.pos[3 * (o0 + e) + 1], blo[1], scale[1]),
+                                  dev::cell10(p.pos[3 * (o0 + e) + 2], blo[2], scale[2]));
             k = ((unsigned long long)code << 13) | (unsigned long long)e;
         }
         keys[e] = k;
@@ -266,7 +266,7 @@ __device__ __forceinline__ bool near_boxes(const float *wb, const float *tb, flo
 // Forces on the slots of one chunk of the CTA's range [.., a1) from all
 // slots of the system [0, n).  BT threads form G = BT / L groups of L lanes;
 // group g holds the 2 consecutive slots c0 + 2g, c0 + 2g + 1 (so a warp's
-// i-particles are contiguous in Morton order) and its lanes split the
+// i-particles are contiguous in Hilbert order) and its lanes split the
 // j-quads of every 64-slot chunk.  Per (warp, 64-slot j-chunk) the warp
 // takes the single-float displacement when the boxes are well separated.
 template <int BT, int POL>
@@ -542,7 +542,7 @@ static int launch_batched_cs(const BatchedParams &p, cudaStream_t st) {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(BT, 1, 1);
-    cfg.dynamicSmemBytes = 8 * kBMaxN;  // Morton keys of one system
+    cfg.dynamicSmemBytes = 8 * kBMaxN;  // Hilbert keys of one system
     {
         const int rc = smem_optin(reinterpret_cast<const void *>(kern), 8 * (size_t)kBMaxN);
         if (rc != NB_OK) return rc;

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "nb_device.cuh"
+#include "nb_order.cuh"
 #include "nb_internal.h"
 #include "nb_sym_core.cuh"
 
@@ -19,7 +20,7 @@ using namespace symcore;
 // ================================================================ batched
 // Many independent systems (offsets [B+1], eps [B]), each unordered pair of
 // a system evaluated once as above, at warp granularity.  Every system is
-// padded to whole 128-slot blocks in Morton order (re-sorted every 16 steps);
+// padded to whole 128-slot blocks in Hilbert order (re-sorted every 16 steps);
 // a work item is (system c, i-block a, j-blocks [b0, b1)) with b0 >= a and at
 // most 8 j-blocks.  Persistent warps take items from an atomic queue ordered
 // largest first; a warp holds its i-block in registers (4 slots per lane),
@@ -32,7 +33,7 @@ using namespace symcore;
 constexpr int BW = 128;           // slots per warp block
 constexpr int BG = 8;             // j-blocks per item at most
 constexpr int kBsMaxN = 8192;     // particles per system (64 blocks)
-constexpr int kBsResort = 16;     // steps between Morton re-sorts
+constexpr int kBsResort = 16;     // steps between Hilbert re-sorts
 
 struct BsParams {
     int32_t B;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
     }
 }
 
-// Morton order of each system (one CTA per system): FP64 bounding box,
+// Hilbert order of each system (one CTA per system): FP64 bounding box,
 // 30-bit codes, keys code << 13 | source index, shared-memory bitonic sort;
 // then the state is gathered into the other buffer in the new order: from
 // the caller's arrays (from_user: particle order) or from the current
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(512) bsym_sort_kernel(BsParams p, int from_use
     for (int e = tid; e < P2; e += blockDim.x) {
         unsigned long long k = ~0ull;
         if (e < n) {
-            uint32_t code = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) code |= dev::morton_part(xsrc(e, d), blo[d], scale[d]) << d;
+            const uint32_t code = dev::hilbert30(dev::cell10(xsrc(e, 0), blo[0], scale[0]),
+                                                 dev::cell10(xsrc(e, 1), blo[1], scale[1]),
+                                                 dev::cell10(xsrc(e, 2), blo[2], scale[2]));
             k = ((unsigned long long)code << 13) | (unsigned long long)e;
         }
         keys[e] = k;

@@ -90,43 +90,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// ---------------------------------------------------------- Morton order
-// Spreads the low 10 bits of v so that bit k lands at bit 3k.
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) r |= ((v >> k) & 1u) << (3 * k);
-    return r;
-}
-
-// One coordinate's share of a 30-bit Morton code: (x - lo) * scale clamped
-// to the 1024 cells [0, 1023], bits spread to every third position.
-__device__ __forceinline__ uint32_t morton_part(double x, double lo, double scale) {
-    double q = (x - lo) * scale;
-    q = q < 0.0 ? 0.0 : (q > 1023.0 ? 1023.0 : q);
-    return spread3((uint32_t)q);
-}
-
-// Ascending bitonic sort of P (a power of two) 64-bit keys in shared memory
-// by the whole CTA (every thread calls it; it ends with a barrier).
-__device__ __forceinline__ void block_bitonic_sort(unsigned long long *keys, int P) {
-    for (int k = 2; k <= P; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int e = threadIdx.x; e < P; e += blockDim.x) {
-                const int x = e ^ j;
-                if (x > e) {
-                    const bool asc = (e & k) == 0;
-                    const unsigned long long a = keys[e], b = keys[x];
-                    if ((a > b) == asc) {
-                        keys[e] = b;
-                        keys[x] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-}
-
 // ------------------------------------------------------------ pair loop
 // Two j-particles (packed in the .x/.y halves) against IR i-particles.
 // The displacement is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) when SPLIT.

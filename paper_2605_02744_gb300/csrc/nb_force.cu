@@ -80,7 +80,7 @@ struct ForceParams {
     uint32_t *counters;
     uint32_t *status;
     long long timeout;
-    // adaptive displacement (NF): particles packed in Morton order
+    // adaptive displacement (NF): particles packed in Hilbert order
     const float *tile_box;   // [N/64][8]: lo[3] hi[3] max|x| pad, per 64 j-slots
     const float *block_box;  // [N/(32 IR)][8], per warp's 32 IR i-slots
     const int *perm;         // packed slot -> particle index
@@ -89,7 +89,7 @@ struct ForceParams {
 
 // Packed slot of register row k of thread tid in i-block b.  The adaptive
 // path (NF) gives each warp 32*IR contiguous slots, so a warp's particles
-// share one small box in the Morton-sorted pack; otherwise rows are strided
+// share one small box in the Hilbert-sorted pack; otherwise rows are strided
 // by the CTA width (coalesced loads and stores).
 template <int NT, int IR, bool NF>
 __device__ __forceinline__ int64_t slot_of(int64_t b, int k, int tid) {

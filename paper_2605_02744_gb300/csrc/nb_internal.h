@@ -66,7 +66,7 @@ struct WsLayout {
     size_t packA;     // float SoA [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
     size_t packB;     // float SoA [4][Np]: VJP cotangents (cx, cy, cz, pbar/3)
     size_t cot64;     // double SoA [4][Np]: the same cotangents in FP64
-    size_t sortbuf;   // Morton keys, permutation, tile/block boxes (adaptive path)
+    size_t sortbuf;   // Hilbert keys, permutation, tile/block boxes (adaptive path)
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
     size_t sym_p;     // symmetric-pair path: FP32 j-side partials per block pair
@@ -109,8 +109,8 @@ struct ForceJob {
     double kick;
     int precision;
     bool split;         // hi/lo displacement (nb_positions resolved)
-    bool adaptive;      // Morton-sorted pack, hi/lo only for near tile pairs
-    bool reuse_order;   // adaptive: keep the previous call's Morton order
+    bool adaptive;      // Hilbert-sorted pack, hi/lo only for near tile pairs
+    bool reuse_order;   // adaptive: keep the previous call's Hilbert order
     float gamma;        // near/far threshold of the adaptive path
     bool packed_ready;  // packA already holds float positions of `pos`
     bool sym;           // symmetric-pair evaluation (nb_pairs resolved)
@@ -124,7 +124,7 @@ struct ForceJob {
 // Resolves nb_opts::positions for a precision: true = split hi/lo.
 bool positions_split(const nb_opts *opts);
 // true when the split displacement is applied only to near tile pairs of a
-// Morton-sorted pack (explicit NB_POS_ADAPTIVE, or the default from N >= 2^16
+// Hilbert-sorted pack (explicit NB_POS_ADAPTIVE, or the default from N >= 2^16
 // for the KAHAN and F64ACC policies; 1/64 is the default near_gamma).
 bool positions_adaptive(const nb_opts *opts, int64_t N, bool stepping = false);
 // Steps of one nb_step call between full re-sorts of the adaptive path.
@@ -158,7 +158,7 @@ inline size_t sortbuf_bytes(int64_t Np) {
     return 8 * (size_t)sort_keys_len(Np) + 4 * (size_t)Np + 32 * (size_t)(Np / 32 + 1) +
            32 * (size_t)(Np / 32 + 1) + 64;
 }
-// reuse_order: the keys already hold a Morton order of these N particles
+// reuse_order: the keys already hold a Hilbert order of these N particles
 // (an earlier call of the same step loop); only the pack and the boxes are
 // redone from the current positions.
 int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t Np, float *soa,

@@ -1,6 +1,6 @@
 // Spatial ordering for the adaptive-displacement force path.
 //
-// Each evaluation sorts the particles along a Morton (Z-order) curve of their
+// Each evaluation sorts the particles along a Hilbert curve of their
 // FP64 positions, packs them in that order, and records an axis-aligned box
 // for every 64 consecutive j-slots and for every warp's i-slots.  Spatially
 // compact groups let the force kernel pick, per (warp, 64-particle sub-tile)
@@ -10,7 +10,7 @@
 //
 //   bbox:     FP64 min/max of the positions (atomics on order-preserving
 //             integer images; min/max do not depend on order)
-//   keys:     30-bit Morton code of the position in that box << 32 | index
+//   keys:     30-bit Hilbert index of the position's cell in that box << 32 | index
 //   sort:     bitonic network on 64-bit keys (shared-memory passes for
 //             strides below 2048, global passes above); keys are unique, so
 //             the order is fully determined
@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "nb_device.cuh"
+#include "nb_order.cuh"
 #include "nb_internal.h"
 
 namespace nb {
@@ -74,7 +75,7 @@ __global__ void bbox_kernel(const double *__restrict__ pos, int64_t N, long long
     }
 }
 
-__global__ void morton_keys_kernel(const double *__restrict__ pos, int64_t N, int64_t P,
+__global__ void hilbert_keys_kernel(const double *__restrict__ pos, int64_t N, int64_t P,
                                    const long long *__restrict__ box,
                                    unsigned long long *__restrict__ keys) {
     double lo[3], scale[3];
@@ -88,9 +89,9 @@ __global__ void morton_keys_kernel(const double *__restrict__ pos, int64_t N, in
          i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long k = ~0ull;
         if (i < N) {
-            uint32_t code = 0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) code |= dev::morton_part(pos[3 * i + c], lo[c], scale[c]) << c;
+            const uint32_t code = dev::hilbert30(dev::cell10(pos[3 * i], lo[0], scale[0]),
+                                  dev::cell10(pos[3 * i + 1], lo[1], scale[1]),
+                                  dev::cell10(pos[3 * i + 2], lo[2], scale[2]));
             k = ((unsigned long long)code << 32) | (unsigned long long)(uint32_t)i;
         }
         keys[i] = k;
@@ -228,7 +229,7 @@ int launch_sorted_pack(const double *pos, const double *mass, int64_t N, int64_t
     const int64_t gb = std::min<int64_t>(cdiv(N, threads), 1024);
     bbox_kernel<<<(unsigned)gb, threads, 0, st>>>(pos, N, box6);
     count_launch();
-    morton_keys_kernel<<<(unsigned)std::min<int64_t>(cdiv(P, threads), 8192), threads, 0, st>>>(
+    hilbert_keys_kernel<<<(unsigned)std::min<int64_t>(cdiv(P, threads), 8192), threads, 0, st>>>(
         pos, N, P, box6, keys);
     count_launch();
     const unsigned nchunks = (unsigned)(P / kSortChunk);

@@ -36,20 +36,20 @@
 // terms per running sum; for F64ACC through an FP32 middle sum in shared
 // memory that goes into FP64 every 16 j-sets, FP64 adds being slow on this
 // part), and stored once per row segment as an FP64 record.  In
-// Morton order a particle's strongest, mutually cancelling terms (its
+// Hilbert order a particle's strongest, mutually cancelling terms (its
 // spatial neighbours) arrive together; with 16 j-sets per flush the FP32
 // running sums of central particles of a log-normal Plummer sphere
 // (N = 300001, eps = 1e-3) lost up to 1e-5 of |a|, with 4 they stay at the
 // 2e-6 of the unsorted order.  A second kernel adds, slot by
 // slot in a fixed order, the records of the row's CTAs and the partials
-// P[I', I] for I' < I, applies G, scatters through the Morton permutation
+// P[I', I] for I' < I, applies G, scatters through the Hilbert permutation
 // and optionally kicks the velocity.  Every
 // sum runs in a fixed order: results are bitwise reproducible.
 //
 // Displacements: single floats, hi/lo pairs (x_j.hi - x_i.hi) +
 // (x_j.lo - x_i.lo), or adaptive: per (warp i-set, j-set) the hi/lo form
 // only when the bounding boxes are closer than gamma * max|x| (a 64-bit
-// mask per warp and item, from the Morton-sorted pack's boxes).
+// mask per warp and item, from the Hilbert-sorted pack's boxes).
 #include <cuda_runtime.h>
 
 #include <algorithm>

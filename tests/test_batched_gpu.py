@@ -1,11 +1,11 @@
 """GPU parity of the batched paths (many independent clusters).
 
 Two paths: the default symmetric-pair path (each unordered pair of a cluster
-once, warp-granular work items, per-cluster Morton order) and the persistent
+once, warp-granular work items, per-cluster Hilbert order) and the persistent
 direct-pair kernel (NB_PAIRS_DIRECT, every compiled thread-block-cluster
 size).  nb_forces_batched against the oracle cluster by cluster (sizes from
 1 to the 8192 maximum), nb_step on a batch against the oracle's leapfrog per
-cluster (across a Morton re-sort), the 512-cluster workload on a sample of
+cluster (across a Hilbert re-sort), the 512-cluster workload on a sample of
 clusters (smallest and largest included) for 10 steps and on small clusters
 for the full 1000 steps with the energy-drift gate, device rejection of an
 invalid cluster, bitwise determinism and graph replay.
@@ -67,7 +67,7 @@ def test_forces_batched_per_cluster(prec, cs, bt, pairs):
 @pytest.mark.parametrize("positions", ["default", "split", "single"])
 @pytest.mark.parametrize("pairs", ["default", "direct"])
 def test_step_batched_matches_oracle_per_cluster(positions, pairs):
-    # 20 steps cross one Morton re-sort of every cluster (every 16 steps)
+    # 20 steps cross one Hilbert re-sort of every cluster (every 16 steps)
     if positions == "single" and pairs == "direct":
         pytest.skip("the direct batched kernel takes hi/lo or adaptive displacements")
     sizes = [64, 65, 200, 1000, 3000, 7, 1, 8192]

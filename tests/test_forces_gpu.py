@@ -89,7 +89,7 @@ def test_every_compiled_shape(shape, cps):
     s = ics.plummer(6000, seed=11)
     _check(s, 0.01, "f64acc", tune=t)
     _check(s, 0.01, "kahan", tune=t)
-    # the adaptive (Morton-sorted) path in the same shape
+    # the adaptive (Hilbert-sorted) path in the same shape
     o = binding.make_opts("kahan", tune=t, positions="adaptive")
     acc = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
     ws = binding.workspace(s.n, 1, o)
@@ -145,7 +145,7 @@ def test_plummer_2pow20_sampled_rows(prec, pairs):
 @pytest.mark.parametrize("n,eps", [(8191, 0.01), (20001, 1e-3), (70001, 1e-3), (300001, 1e-3)])
 @pytest.mark.parametrize("prec", ["kahan", "f64acc"])
 def test_adaptive_positions(n, eps, prec):
-    # Morton-sorted pack, hi/lo displacement only for near tile pairs
+    # Hilbert-sorted pack, hi/lo displacement only for near tile pairs
     s = ics.plummer_lognormal(n, seed=n)
     o = binding.make_opts(prec, positions="adaptive")
     acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")

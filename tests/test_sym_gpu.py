@@ -4,7 +4,7 @@ Each unordered pair is evaluated once and applied to both particles (Eq. 1
 changes sign under i <-> j apart from the masses).  Covered: 1, 2, 3 and 17
 row blocks of 2048 slots with ragged last blocks, the three displacement
 modes and three FP32-pair policies, the fold of j-side partials and row
-records, the fused closing half-kick of a step loop (and the Morton order
+records, the fused closing half-kick of a step loop (and the Hilbert order
 kept across steps), G scaling, a missing potential output, run-to-run
 bitwise determinism, agreement with the direct path, and the host-side
 refusals (eps = 0, a workspace sized for the direct path).
@@ -88,7 +88,7 @@ def test_bitwise_determinism_and_direct_agreement():
 @pytest.mark.parametrize("n,steps", [(5000, 12), (40000, 20)])
 def test_step_loop_matches_oracle(n, steps):
     # the closing half-kick is fused into the fold; 40000 particles step on
-    # the Morton-sorted pack, re-sorted every 16 steps
+    # the Hilbert-sorted pack, re-sorted every 16 steps
     s = ics.plummer(n, seed=7)
     eps, h = 2e-3, 1e-4
     g = api.System(s.pos, s.vel, s.mass, eps, precision="f64acc", pairs="symmetric")
