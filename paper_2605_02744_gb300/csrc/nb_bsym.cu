@@ -399,15 +399,25 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
 #pragma unroll
         for (int v = 0; v < 16; ++v) tot[w][v][l].zero();
         const int nq = (b1 - b0) * 4;  // j-sets of the item (<= 32)
-        unsigned near = 0u;
+        // near masks of the warp's two 64-slot halves (packed groups 0, 1)
+        unsigned near0 = 0u, near1 = 0u;
         if (MODE == 2) {
-            float wbx[7], tb[7];
+            float hb[2][7], tb[7];
 #pragma unroll
-            for (int d = 0; d < 7; ++d) wbx[d] = __ldg(p.box128 + (ib / BW) * 8 + d);
+            for (int h = 0; h < 2; ++h) {
+                const float *a = p.box32 + (ib / JS + 2 * h) * 8, *c = a + 8;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    hb[h][d] = fminf(__ldg(a + d), __ldg(c + d));
+                    hb[h][3 + d] = fmaxf(__ldg(a + 3 + d), __ldg(c + 3 + d));
+                }
+                hb[h][6] = fmaxf(__ldg(a + 6), __ldg(c + 6));
+            }
             const int64_t js = (sb + (int64_t)BW * b0) / JS + (l < nq ? l : 0);
 #pragma unroll
             for (int d = 0; d < 7; ++d) tb[d] = __ldg(p.box32 + js * 8 + d);
-            near = __ballot_sync(0xffffffffu, l < nq && boxes_near(wbx, tb, p.gamma));
+            near0 = __ballot_sync(0xffffffffu, l < nq && boxes_near(hb[0], tb, p.gamma));
+            near1 = __ballot_sync(0xffffffffu, l < nq && boxes_near(hb[1], tb, p.gamma));
         }
         float jn[7];
         const int64_t jb0 = sb + (int64_t)BW * b0;
@@ -421,14 +431,14 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
 #pragma unroll
                 for (int d = 0; d < 7; ++d) jn[d] = __ldg(p.soa + d * p.Ns + jb0 + JS * (q + 1) + l);
             const int b = b0 + (q >> 2);
-            const bool nqb = (near >> q) & 1u;
+            const int nqb = (int)((near0 >> q) & 1u) | ((int)((near1 >> q) & 1u) << 1);
             float4 bs;
             if (b != a) {
-                run_set<MODE, true, POT>(S, e2, jc, nqb, bs, -1);
+                run_set2<MODE, true, POT>(S, e2, jc, nqb, bs, -1);
                 const int64_t pair = p.pbase[c] + (int64_t)b * (b - 1) / 2 + a;
                 __stcs(reinterpret_cast<float4 *>(p.P) + pair * BW + 32 * (q & 3) + l, bs);
             } else {
-                run_set<MODE, false, POT>(S, e2, jc, nqb, bs, q & 3);
+                run_set2<MODE, false, POT>(S, e2, jc, nqb, bs, q & 3);
             }
             if ((q & 3) == 3) {
 #pragma unroll

@@ -44,11 +44,12 @@ struct ISet {
     float2 ax[2], ay[2], az[2], ph[2];
 };
 
-// One rotation step: the lane's four i-slots against its current j.  With
-// SELF, i-slot self_k is the j-particle itself: its half of the pair gets a
-// zero mass (Eq. 1 leaves out j = i).  POT: also the potential sums (2 of
-// the 18 FP32 operations per unordered pair).
-template <bool NEAR, bool SYM, bool SELF, bool POT>
+// One rotation step: the lane's four i-slots against its current j.  NEAR:
+// bit g set = packed group g (i-slots 2g, 2g + 1) takes the hi/lo
+// displacement.  With SELF, i-slot self_k is the j-particle itself: its half
+// of the pair gets a zero mass (Eq. 1 leaves out j = i).  POT: also the
+// potential sums (2 of the 18 FP32 operations per unordered pair).
+template <int NEAR, bool SYM, bool SELF, bool POT>
 __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float jy, float jz,
                                      float jm, float jxl, float jyl, float jzl, float &bx,
                                      float &by, float &bz, float &bp, int self_k = -1) {
@@ -60,7 +61,7 @@ __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float j
         float2 dx = add2(X, S.nx[g]);
         float2 dy = add2(Y, S.ny[g]);
         float2 dz = add2(Z, S.nz[g]);
-        if (NEAR) {
+        if ((NEAR >> g) & 1) {
             dx = add2(dx, add2(f2(jxl, jxl), S.nxl[g]));
             dy = add2(dy, add2(f2(jyl, jyl), S.nyl[g]));
             dz = add2(dz, add2(f2(jzl, jzl), S.nzl[g]));
@@ -94,7 +95,7 @@ __device__ __forceinline__ void step(ISet &S, const float2 e2, float jx, float j
 // 32 steps over one j-set; the j values (and sums) end on their home lane.
 // self_k >= 0 (diagonal items only): the j-set is the warp's own i-slots
 // 32 self_k + [0, 32), so step 0 pairs every lane with itself.
-template <bool NEAR, bool SYM, bool POT>
+template <int NEAR, bool SYM, bool POT>
 __device__ __forceinline__ void rotate_set(ISet &S, const float2 e2, const float (&j)[7],
                                            float4 &b, int self_k) {
     const int src = (threadIdx.x + 1) & 31;
@@ -105,7 +106,7 @@ __device__ __forceinline__ void rotate_set(ISet &S, const float2 e2, const float
         jy = __shfl_sync(0xffffffffu, jy, src);
         jz = __shfl_sync(0xffffffffu, jz, src);
         jm = __shfl_sync(0xffffffffu, jm, src);
-        if (NEAR) {
+        if (NEAR != 0) {
             jxl = __shfl_sync(0xffffffffu, jxl, src);
             jyl = __shfl_sync(0xffffffffu, jyl, src);
             jzl = __shfl_sync(0xffffffffu, jzl, src);
@@ -135,9 +136,23 @@ template <int MODE, bool SYM, bool POT>
 __device__ __forceinline__ void run_set(ISet &S, const float2 e2, const float (&j)[7], bool near,
                                         float4 &b, int self_k) {
     if (MODE == 1 || (MODE == 2 && near))
-        rotate_set<true, SYM, POT>(S, e2, j, b, self_k);
+        rotate_set<3, SYM, POT>(S, e2, j, b, self_k);
     else
-        rotate_set<false, SYM, POT>(S, e2, j, b, self_k);
+        rotate_set<0, SYM, POT>(S, e2, j, b, self_k);
+}
+
+// The same with a separate near/far choice for the two packed groups (the
+// warp's 64-slot halves): near2 bit g = group g near.
+template <int MODE, bool SYM, bool POT>
+__device__ __forceinline__ void run_set2(ISet &S, const float2 e2, const float (&j)[7], int near2,
+                                         float4 &b, int self_k) {
+    const int m = MODE == 1 ? 3 : (MODE == 2 ? near2 : 0);
+    switch (m) {
+        case 0: rotate_set<0, SYM, POT>(S, e2, j, b, self_k); break;
+        case 1: rotate_set<1, SYM, POT>(S, e2, j, b, self_k); break;
+        case 2: rotate_set<2, SYM, POT>(S, e2, j, b, self_k); break;
+        default: rotate_set<3, SYM, POT>(S, e2, j, b, self_k); break;
+    }
 }
 
 // Adds an FP64 record value in the policy's arithmetic.
