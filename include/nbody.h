@@ -117,6 +117,12 @@ typedef struct nb_tune {
     int32_t stages;       /* depth of the bulk-copy ring: 2..4               */
     int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..4                    */
     int32_t cluster_ctas; /* batched kernel: CTAs per thread-block cluster, 2/4/8 */
+    int32_t item_blocks;  /* batched symmetric path: 128-particle j-blocks per
+                             work item, 2/4/8 (0 = 8).  Smaller items balance
+                             the queue's tail but write more 4 KiB FP64
+                             records: the workspace provisions 6, 10 or 18
+                             items per 128 particles for 8, 4 or 2; other
+                             values are refused (NB_ERR_INVALID) */
 } nb_tune;
 
 typedef struct nb_opts {

@@ -100,10 +100,12 @@ class System:
                                      lambda: T.autotune_forces(self.pos, self.mass, eps,
                                                                precision))
             else:
-                tune = _resolve_tune(tune, "batched", precision, n,
+                kind = "batched-" + T.batched_pairs(precision, pairs)
+                tune = _resolve_tune(tune, kind, precision, n,
                                      lambda: T.autotune_batched(self.pos, self.vel, self.mass,
                                                                 offsets, eps, 1e-3,
-                                                                precision=precision))
+                                                                precision=precision,
+                                                                pairs=pairs))
         self.acc = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
         self.pot = torch.zeros(n, dtype=torch.float64, device=self.device)
         self.opts = B.make_opts(precision, G, stream, use_graph=use_graph, tune=tune,

@@ -60,7 +60,8 @@ class NbLibraryMissing(RuntimeError):
 class nb_tune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("i_per_thread", ctypes.c_int32),
                 ("tile_j", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
+                ("item_blocks", ctypes.c_int32)]
 
 
 class nb_opts(ctypes.Structure):

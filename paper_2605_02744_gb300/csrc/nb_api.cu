@@ -154,11 +154,16 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     }
     if (bsym_wanted(opts, N, B)) {
         L.bsym = off;
-        L.bsym_bytes = bsym_layout(N, B).bytes;
+        L.bsym_bytes = bsym_layout(N, B, bsym_item_blocks(opts)).bytes;
         off = align256(off + L.bsym_bytes);
     }
     L.total = off;
     return L;
+}
+
+int bsym_item_blocks(const nb_opts *o) {
+    const int g = (o && o->tune) ? o->tune->item_blocks : 0;
+    return g == 0 ? 8 : ((g == 2 || g == 4 || g == 8) ? g : 0);
 }
 
 bool bsym_wanted(const nb_opts *o, int64_t N, int32_t B) {
@@ -324,6 +329,7 @@ int nb_tune_valid(const nb_tune *t) {
     nb_opts o;
     nb_opts_default(&o);
     o.tune = t;
+    if (bsym_item_blocks(&o) == 0) return 0;
     Shape s;
     return resolve_shape(&o, 1 << 20, kKindForce, &s) ? 1 : 0;
 }
@@ -377,6 +383,7 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
     j.threads = o->tune ? o->tune->threads : 0;
+    j.item_blocks = o->tune ? o->tune->item_blocks : 0;
     j.positions = o->positions;
     j.gamma = o->near_gamma;
     j.sym = bsym_wanted(o, N, B);
@@ -406,6 +413,7 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
     j.precision = o->precision;
     j.cluster = o->tune ? o->tune->cluster_ctas : 0;
     j.threads = o->tune ? o->tune->threads : 0;
+    j.item_blocks = o->tune ? o->tune->item_blocks : 0;
     j.positions = o->positions;
     j.gamma = o->near_gamma;
     j.sym = bsym_wanted(o, s->N, s->B);
@@ -508,6 +516,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
             key.t.stages = o->tune->stages;
             key.t.ctas_per_sm = o->tune->ctas_per_sm;
             key.t.cluster_ctas = o->tune->cluster_ctas;
+            key.t.item_blocks = o->tune->item_blocks;
         }
         cudaGetDevice(&key.device);
         cudaGraphExec_t exec = nullptr;

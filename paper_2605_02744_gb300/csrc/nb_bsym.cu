@@ -31,7 +31,7 @@ using namespace symcore;
 // its row and the partials of the blocks a' < a, so results do not depend on
 // which warp took which item.
 constexpr int BW = 128;           // slots per warp block
-constexpr int BG = 8;             // j-blocks per item at most
+constexpr int BG = 8;             // j-blocks per item at most (default item width)
 constexpr int kBsMaxN = 8192;     // particles per system (64 blocks)
 constexpr int kBsResort = 16;     // steps between Hilbert re-sorts
 
@@ -59,6 +59,7 @@ struct BsParams {
     float *P;            // [block pairs][128][4]
     double *rec;         // [items][128][4]
     int64_t items_cap, pairs_cap;
+    int32_t g;           // j-blocks per item at most: 2, 4 or BG
     float gamma;
     uint32_t *status;
     // FP64 state in slot order for the whole call (contiguous kick, drift,
@@ -73,8 +74,8 @@ __device__ __forceinline__ double *st_arr(const BsParams &p, int b, int k) {
     return p.st[b] + (int64_t)k * p.Ns;
 }
 
-__device__ __forceinline__ int64_t bs_items_of_row(int64_t nblk, int64_t a) {
-    return (nblk - a + BG - 1) / BG;
+__device__ __forceinline__ int64_t bs_items_of_row(int64_t nblk, int64_t a, int g) {
+    return (nblk - a + g - 1) / g;
 }
 
 // Validation, padded layout, item list and its largest-first order (one
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
             for (int64_t a = 0; a < nblk; ++a) {
                 p.rstart[blk + a] = (int32_t)(ib + it);
                 p.bsys[blk + a] = c;
-                it += bs_items_of_row(nblk, a);
+                it += bs_items_of_row(nblk, a, p.g);
             }
             sb += nblk * BW;
             ib += it;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
         p.ibase[p.B] = ib;
         p.pbase[p.B] = pb;
         p.rstart[blk] = (int32_t)ib;
-        if (sb > p.Ns || ib > p.items_cap || pb > p.pairs_cap) {
+        if (sb > p.Ns || ib > p.items_cap || pb > p.pairs_cap || p.g < 1 || p.g > BG) {
             // cannot happen (bounds of bsym_layout); if it did, every system
             // becomes empty so that no kernel indexes past the buffers
             dev::set_status(p.status, kStatusInvalid);
@@ -138,8 +139,8 @@ __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N)
         const int64_t nblk = (p.sbase[c + 1] - p.sbase[c]) / BW;
         int64_t idx = p.ibase[c];
         for (int64_t a = 0; a < nblk; ++a)
-            for (int64_t b0 = a; b0 < nblk; b0 += BG)
-                p.items[idx++] = make_int4(c, (int)a, (int)b0, (int)(b0 + BG < nblk ? b0 + BG : nblk));
+            for (int64_t b0 = a; b0 < nblk; b0 += p.g)
+                p.items[idx++] = make_int4(c, (int)a, (int)b0, (int)(b0 + p.g < nblk ? b0 + p.g : nblk));
     }
     __syncthreads();
     // stable counting sort by size (j-blocks), largest first: per-thread
@@ -575,11 +576,14 @@ int launch_bsym_pol(BsParams p, const BatchedJob &j, int mode, int64_t nb_max) {
 }  // namespace
 
 // ------------------------------------------------------------ batched host
-BsymLayout bsym_layout(int64_t N, int32_t B) {
+BsymLayout bsym_layout(int64_t N, int32_t B, int g) {
     BsymLayout z{};
+    if (g < 1 || g > BG) g = BG;
     z.Ns = round_up(N + (int64_t)BW * B, BW);
     z.blocks = z.Ns / BW;
-    z.items = 6 * z.blocks;                 // per system <= nblk (1 + 65 / 16) items
+    // a system of n <= 64 blocks has sum over rows of ceil(m / g), m = 1..n,
+    // items: <= n (n + 1) / (2 g) + n <= n (65 / (2 g) + 1)
+    z.items = (65 / (2 * g) + 2) * z.blocks;
     z.pairs = (int64_t)(BW / 2) * z.blocks;  // per system nblk (nblk - 1) / 2 <= 32 nblk
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -610,7 +614,10 @@ BsymLayout bsym_layout(int64_t N, int32_t B) {
 
 int launch_batched_sym(const BatchedJob &j) {
     if (j.L.bsym_bytes == 0) return fail(NB_ERR_WORKSPACE, "workspace has no batched symmetric buffers");
-    const BsymLayout z = bsym_layout(j.N, j.B);
+    const int g = j.item_blocks == 0 ? BG : j.item_blocks;
+    if (g != 2 && g != 4 && g != BG)
+        return fail(NB_ERR_INVALID, "item_blocks must be 2, 4 or 8 (got %d)", j.item_blocks);
+    const BsymLayout z = bsym_layout(j.N, j.B, g);
     char *base = j.ws + j.L.bsym;
     BsParams p;
     p.B = j.B;
@@ -644,6 +651,7 @@ int launch_batched_sym(const BatchedJob &j) {
     p.cur = 0;
     p.items_cap = z.items;
     p.pairs_cap = z.pairs;
+    p.g = g;
     p.gamma = j.gamma > 0.f ? j.gamma : kNearFarGamma;
     p.status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     const int mode = j.positions == NB_POS_SPLIT ? 1 : (j.positions == NB_POS_SINGLE ? 0 : 2);

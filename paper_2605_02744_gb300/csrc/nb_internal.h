@@ -278,6 +278,7 @@ struct BatchedJob {
     int precision;
     int cluster;      // CTAs per thread-block cluster (0 = default)
     int threads;      // threads per CTA (0 = default)
+    int item_blocks;  // symmetric path: j-blocks per work item (0 = default)
     int positions;    // nb_positions: SPLIT = hi/lo everywhere, else adaptive
     float gamma;      // near/far threshold (0 = default)
     bool sym;         // symmetric pairs (nb_pairs resolved)
@@ -289,14 +290,17 @@ struct BatchedJob {
 int launch_batched(const BatchedJob &job);
 size_t batched_scratch_bytes(int32_t B);
 
-// Batched symmetric-pair path (nb_sym.cu): the workspace region's layout for
-// N particles in B systems (bounds from N and B only).
+// Batched symmetric-pair path (nb_bsym.cu): the workspace region's layout for
+// N particles in B systems cut into items of up to g j-blocks (bounds from
+// N, B and g only); g = bsym_item_blocks(opts) is 2, 4 or 8, 0 if the tune
+// asks for another width.
 struct BsymLayout {
     int64_t Ns, blocks, items, pairs;
     size_t o_sbase, o_ibase, o_pbase, o_rstart, o_bsys, o_items, o_order, o_misc, o_soa, o_perm,
         o_box32, o_box128, o_P, o_rec, o_st0, o_st1, o_pots, bytes;
 };
-BsymLayout bsym_layout(int64_t N, int32_t B);
+BsymLayout bsym_layout(int64_t N, int32_t B, int g);
+int bsym_item_blocks(const nb_opts *opts);
 bool bsym_wanted(const nb_opts *opts, int64_t N, int32_t B);
 int launch_batched_sym(const BatchedJob &job);
 

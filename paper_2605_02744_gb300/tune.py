@@ -1,8 +1,9 @@
 """Launch-shape autotuner with a JSON cache.
 
 For the single-system kernels a candidate is an nb_tune (threads, i-particles
-per thread, j-tile, bulk-copy stages, persistent CTAs per SM); for the
-batched kernel it is the thread-block-cluster size.  Every candidate this
+per thread, j-tile, bulk-copy stages, persistent CTAs per SM); for batches it
+is the work-item width in j-blocks (symmetric pairs, the default) or the
+thread-block-cluster size (direct pairs).  Every candidate this
 build compiled (``nb_tune_valid``) is timed on the caller's inputs with CUDA
 events after a warm-up; the fastest median wins, ties going to the smaller
 resource use.  Results are cached per (device name, compute capability,
@@ -29,6 +30,7 @@ FORCE_CANDIDATES = [
     for c in (1, 2, 4)
 ]
 BATCHED_CANDIDATES = [dict(cluster_ctas=c, threads=t) for c in (2, 4, 8) for t in (256, 512)]
+BATCHED_SYM_CANDIDATES = [dict(item_blocks=g) for g in (2, 4, 8)]
 VJP_CANDIDATES = [
     dict(threads=t, i_per_thread=i, tile_j=j, stages=s, ctas_per_sm=4)
     for (t, i, j, s) in [(128, 2, 128, 3), (256, 2, 128, 3), (256, 1, 128, 3), (128, 1, 64, 2)]
@@ -95,8 +97,15 @@ def _median_ms(fn, reps: int) -> float:
 
 def _cost(t: dict) -> tuple:
     # tie-break: fewer threads x i-per-thread, then fewer stages, then CTAs
+    # (wider batched items: fewer records, less workspace)
     return (t.get("threads", 0) * t.get("i_per_thread", 0), t.get("stages", 0),
-            t.get("ctas_per_sm", 0), t.get("cluster_ctas", 0))
+            t.get("ctas_per_sm", 0), t.get("cluster_ctas", 0), -t.get("item_blocks", 0))
+
+
+def batched_pairs(precision: str, pairs: str = "default") -> str:
+    """The pair path a batched call takes: "symmetric" unless direct pairs are
+    asked for or the pairs are FP64 (which only the direct kernel computes)."""
+    return "direct" if pairs == "direct" or precision == "fp64" else "symmetric"
 
 
 def autotune_forces(pos, mass, eps: float, precision="kahan", reps: int = 5, warmup: int = 2,
@@ -131,19 +140,26 @@ def autotune_forces(pos, mass, eps: float, precision="kahan", reps: int = 5, war
 
 def autotune_batched(pos, vel, mass, offsets, eps, dt: float, nsteps: int = 20,
                      precision="f64acc", reps: int = 3, candidates=None,
-                     store: bool = True) -> dict:
-    """Time nsteps batched KDK steps per cluster size; returns the best nb_tune dict.
+                     store: bool = True, pairs: str = "default") -> dict:
+    """Time nsteps batched KDK steps per candidate; returns the best nb_tune dict.
 
-    The candidates are shapes of the direct batched kernel (NB_PAIRS_DIRECT),
-    which is what is timed; the symmetric batched path has no shape
-    parameters.
+    The candidates are those of the path `pairs` resolves to (batched_pairs):
+    the work-item width of the symmetric path, or the cluster size and CTA
+    threads of the direct kernel.  The result is cached under the kind
+    "batched-symmetric" or "batched-direct".
     """
     from .api import System
     n = mass.shape[0]
+    path = batched_pairs(precision, pairs)
+    default = BATCHED_SYM_CANDIDATES if path == "symmetric" else BATCHED_CANDIDATES
     results = []
-    for cand in candidates or BATCHED_CANDIDATES:
-        sysm = System(pos, vel, mass, eps, offsets=offsets, precision=precision, tune=cand,
-                      device=pos.device if torch.is_tensor(pos) else "cuda", pairs="direct")
+    device = pos.device if torch.is_tensor(pos) else "cuda"
+    for cand in candidates or default:
+        # the trial runs step copies: the caller's state is left as it was
+        sysm = System(torch.as_tensor(pos, dtype=torch.float64, device=device).clone(),
+                      torch.as_tensor(vel, dtype=torch.float64, device=device).clone(), mass, eps,
+                      offsets=offsets, precision=precision, tune=cand, device=device,
+                      pairs=path)
         sysm.step(dt, 1)
         t = _median_ms(lambda: sysm.step(dt, nsteps), reps)
         results.append((t, _cost(cand), cand))
@@ -151,7 +167,7 @@ def autotune_batched(pos, vel, mass, offsets, eps, dt: float, nsteps: int = 20,
     results.sort(key=lambda r: (r[0], r[1]))
     best = results[0]
     if store:
-        _store(_key("batched", precision, n),
+        _store(_key("batched-" + path, precision, n),
                {"tune": best[2], "ms": best[0],
                 "all": [{"tune": c, "ms": t} for t, _, c in results]})
     return best[2]

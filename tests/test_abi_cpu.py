@@ -182,3 +182,29 @@ def test_batched_symmetric_workspace(B):
     slots = n + 128 * b
     assert sym - direct >= 2 * 80 * slots  # two slot-order FP64 state buffers
     assert B.nb_workspace_bytes(2 * n, b, _opts(B)) > sym
+
+
+def test_batched_item_width(B):
+    # nb_tune.item_blocks: 2, 4 or 8 j-blocks per symmetric batched work item
+    # (0 = 8); each item owns a 4 KiB FP64 record, provisioned for 18, 10 or
+    # 6 items per 128-slot block
+    for g in (0, 2, 4, 8):
+        assert B.nb_tune_valid({"item_blocks": g})
+    for g in (1, 3, 16, -2):
+        assert not B.nb_tune_valid({"item_blocks": g})
+    n, b = 100000, 64
+    blocks = -(-(n + 128 * b) // 128)
+
+    def ws(g):
+        t = B.nb_tune(item_blocks=g)
+        o = _opts(B, tune=ctypes.pointer(t))
+        return B.nb_workspace_bytes(n, b, o)
+
+    assert ws(0) == ws(8) == B.nb_workspace_bytes(n, b, _opts(B))
+    assert ws(4) - ws(8) >= 4 * blocks * 4096
+    assert ws(2) - ws(8) >= 12 * blocks * 4096
+    # the direct path ignores the field
+    t = B.nb_tune(item_blocks=2)
+    d = _opts(B, pairs=B.NB_PAIRS_DIRECT, tune=ctypes.pointer(t))
+    assert B.nb_workspace_bytes(n, b, d) == B.nb_workspace_bytes(
+        n, b, _opts(B, pairs=B.NB_PAIRS_DIRECT))

@@ -1,7 +1,8 @@
 """GPU parity of the batched paths (many independent clusters).
 
 Two paths: the default symmetric-pair path (each unordered pair of a cluster
-once, warp-granular work items, per-cluster Hilbert order) and the persistent
+once, warp-granular work items of 2, 4 or 8 j-blocks, per-cluster Hilbert
+order) and the persistent
 direct-pair kernel (NB_PAIRS_DIRECT, every compiled thread-block-cluster
 size).  nb_forces_batched against the oracle cluster by cluster (sizes from
 1 to the 8192 maximum), nb_step on a batch against the oracle's leapfrog per
@@ -40,14 +41,13 @@ def _eps(b, seed=0):
 
 
 @pytest.mark.parametrize("prec", ["f64acc", "kahan"])
-@pytest.mark.parametrize("cs,bt,pairs", [(2, 256, "direct"), (4, 256, "direct"),
-                                         (8, 256, "direct"), (2, 512, "direct"),
-                                         (4, 512, "direct"), (8, 512, "direct"),
-                                         (0, 0, "symmetric")])
-def test_forces_batched_per_cluster(prec, cs, bt, pairs):
+@pytest.mark.parametrize("tune,pairs", [({"cluster_ctas": c, "threads": t}, "direct")
+                                        for t in (256, 512) for c in (2, 4, 8)]
+                         + [(None, "symmetric"), ({"item_blocks": 2}, "symmetric"),
+                            ({"item_blocks": 4}, "symmetric")])
+def test_forces_batched_per_cluster(prec, tune, pairs):
     s = _batch(SIZES)
     eps = _eps(len(SIZES))
-    tune = {"cluster_ctas": cs, "threads": bt} if cs else None
     opts = binding.make_opts(prec, tune=tune, pairs=pairs)
     n = s.n
     acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
@@ -234,3 +234,43 @@ def test_symmetric_batched_thousands_of_tiny_clusters():
         ra, rp = oracle.forces(s.pos[lo:hi], s.mass[lo:hi], eps[c])
         assert rel_vec_err(a[lo:hi], ra).max() <= 1e-5, c
         assert rel_err(p[lo:hi], rp).max() <= 1e-5, c
+
+
+@pytest.mark.parametrize("g", [2, 4])
+def test_symmetric_batched_item_widths_step(g):
+    # narrower work items change only which FP32 sums become FP64 records:
+    # 20 steps (one re-sort) against the oracle's leapfrog and the default width
+    sizes = [8192, 64, 65, 1000, 3000, 1, 200]
+    s = _batch(sizes, seed=21)
+    eps = _eps(len(sizes), 8)
+    out = {}
+    for tune in (None, {"item_blocks": g}):
+        sysm = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision="f64acc",
+                          tune=tune)
+        sysm.step(1e-3, 20)
+        assert sysm.poll() == binding.NB_OK
+        out[g if tune else 8] = (host(sysm.pos), host(sysm.vel), host(sysm.acc))
+    x, v, a = out[g]
+    for c in range(len(sizes)):
+        lo, hi = s.offsets[c], s.offsets[c + 1]
+        xo, vo, ao, _ = oracle.kdk(s.pos[lo:hi], s.vel[lo:hi], s.mass[lo:hi], eps[c], 1e-3, 20)
+        dv = np.abs(vo - s.vel[lo:hi]).max()
+        dx = np.abs(xo - s.pos[lo:hi]).max()
+        assert np.abs(v[lo:hi] - vo).max() <= 1e-5 * dv + 1e-13, c
+        assert np.abs(x[lo:hi] - xo).max() <= 1e-5 * dx + 1e-13, c
+        assert rel_vec_err(a[lo:hi], ao).max() <= 1e-5, c
+    assert rel_vec_err(a, out[8][2]).max() <= 2e-5
+
+
+def test_symmetric_batched_refuses_other_item_widths():
+    sizes = [100, 200]
+    s = _batch(sizes)
+    opts = binding.make_opts("f64acc", tune={"item_blocks": 3})
+    acc = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    ws = binding.workspace(s.n, 2, opts)
+    with pytest.raises(binding.NbError) as e:
+        binding.nb_forces_batched(dev(s.pos), dev(s.mass),
+                                  torch.tensor(s.offsets, device="cuda"), dev(_eps(2)), acc,
+                                  None, ws, opts)
+    assert e.value.code == binding.NB_ERR_INVALID
+    assert np.all(host(acc) == 0.0)
