@@ -11,8 +11,8 @@
  * reordering:
  *
  *   acceleration (Eq. 1 divided by m_i, Sec. 2.1), with Plummer softening
- *   (the softening length "included in the distance computation", App. A,
- *   read as r^2 + eps^2):
+ *   (App. A adds a softening length to the pair distance without giving the
+ *   form; read as r^2 + eps^2):
  *       a_i   =  G sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2}
  *   potential (not printed in the paper; the companion quantity of Eq. 1):
  *       phi_i = -G sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^{1/2}
