@@ -12,7 +12,9 @@ the direct path (timed alongside) every ordered pair.  Alongside: the
 FP64-accumulate variant's rate, the adjoint/forward time ratio of the
 16384-particle, 200-step gradient, the roofline of the step against the FP32
 FMA peak (20 flops per interaction), the end-to-end rate from host buffers,
-and the FP64 oracle timed on the host cores on a sample of rows.
+and the FP64 oracle timed on the host cores on a sample of rows; on those
+exact rows, the relative errors of each timed configuration's forces at the
+initial positions ("accuracy": gated at 1e-5 in the tests).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -162,8 +164,12 @@ def _traffic():
     return float(vals["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in vals else None
 
 
-def cpu_baseline(seconds: float = 10.0):
-    """FP64 oracle rows on the host cores: exact a_i, phi_i for sampled i."""
+def cpu_baseline(seconds: float = 10.0, gpu=None):
+    """FP64 oracle rows on the host cores: exact a_i, phi_i for sampled i.
+
+    `gpu`: {name: (acc [N, 3], pot [N])} from GPU evaluations at the same
+    positions; their errors on the sampled rows are returned as a second
+    value (see accuracy_on_rows)."""
     import numpy as np
 
     import oracle
@@ -178,12 +184,37 @@ def cpu_baseline(seconds: float = 10.0):
     nrows = int(max(64, min(N_MAIN, 64 * seconds / max(dt, 1e-3))))
     rows = rng.choice(N_MAIN, nrows, replace=False)
     t0 = time.perf_counter()
-    oracle.forces_rows(s.pos, s.mass, EPS_MAIN, rows)
+    ra, rp = oracle.forces_rows(s.pos, s.mass, EPS_MAIN, rows)
     el = time.perf_counter() - t0
     rate = nrows * N_MAIN / el / 1e9
-    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    info = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{nrows} exact rows x {N_MAIN} j of the 2^20 Plummer sphere "
                       f"(FP64 C, OpenMP over rows), {el:.1f} s"}
+    acc = None
+    if gpu:
+        acc = {"rows": nrows, "reference": "the FP64 oracle's exact rows above",
+               "gate": 1e-5}
+        for name, (a, p) in gpu.items():
+            acc[name] = accuracy_on_rows(a[rows], p[rows], ra, rp)
+    return info, acc
+
+
+def accuracy_on_rows(a, p, ra, rp):
+    """Relative errors of GPU (a, p) against exact rows (ra, rp): per particle
+    |a - a_ref| / |a_ref| (vector norm; gated at 1e-5) and |p - p_ref| / |p_ref|
+    as max, 99.9th percentile and median; also the component-wise relative
+    deviation (the paper's form, ill-conditioned where a component is near
+    zero) as median and 99th percentile."""
+    import numpy as np
+    e = np.linalg.norm(a - ra, axis=1) / np.linalg.norm(ra, axis=1)
+    ep = np.abs(p - rp) / np.abs(rp)
+    ec = (np.abs(a - ra) / np.abs(ra)).ravel()
+    return {"acc_max": float(e.max()), "acc_p999": float(np.quantile(e, 0.999)),
+            "acc_median": float(np.median(e)), "pot_max": float(ep.max()),
+            "pot_median": float(np.median(ep)),
+            "componentwise_median": float(np.median(ec)),
+            "componentwise_p99": float(np.quantile(ec, 0.99)),
+            "pass": bool(e.max() <= 1e-5 and ep.max() <= 1e-5)}
 
 
 def run_reference(args):
@@ -365,12 +396,14 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     results = {}
+    first = {}  # each configuration's forces at the initial positions (untimed)
     for prec, pairs in (("kahan", "default"), ("f64acc", "default"), ("kahan_direct", "direct")):
         if prec == "kahan_direct" and args.skip_extra:
             continue
         system = api.System(s.pos, s.vel, s.mass, EPS_MAIN, precision=prec.split("_")[0],
                             device=dev, pairs=pairs)
         system.forces()
+        first[prec] = (system.acc.cpu().numpy(), system.pot.cpu().numpy())
         for _ in range(args.warmup):
             system.step(DT_MAIN, 1)
             system.energy()
@@ -508,7 +541,7 @@ def run_ours(args):
         "paper_workload": paper,
     }
     if ws == 1 and not args.skip_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"], line["accuracy"] = cpu_baseline(args.cpu_seconds, first)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
