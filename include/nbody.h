@@ -154,7 +154,8 @@ const char *nb_last_error(void);
  * threads).  Kernels replayed from a captured CUDA graph are not counted. */
 unsigned long long nb_launch_count(void);
 
-/* 1 if `tune` names a kernel shape compiled into this build, else 0. */
+/* 1 if `tune` names a kernel shape compiled into this build (and an
+ * item_blocks of 0, 2, 4 or 8), else 0. */
 int nb_tune_valid(const nb_tune *tune);
 
 /*
@@ -215,7 +216,10 @@ int nb_forces_noalloc(const double *pos, const double *mass, int64_t N, double e
  * clusters follows the SPMD split of Sec. 3.1 (independent work per core):
  * warp-granular work items of every cluster on the symmetric path
  * (default), one cluster per thread-block cluster on the direct path
- * (opts->pairs = NB_PAIRS_DIRECT).
+ * (opts->pairs = NB_PAIRS_DIRECT).  Host-side errors: NB_ERR_INVALID for
+ * B < 1, N < B, N > 2^30, NULL arrays, a non-finite G, an unknown
+ * precision, or (symmetric path) a tune item_blocks other than 0, 2, 4, 8;
+ * NB_ERR_UNSUPPORTED for FP64 pairs; NB_ERR_WORKSPACE if ws is too small.
  */
 int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
                       int64_t N, const double *eps, double *acc, double *pot, void *ws,
