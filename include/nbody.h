@@ -80,8 +80,9 @@ typedef enum {
     NB_POS_SINGLE = 2,
     NB_POS_ADAPTIVE = 3 /* particles sorted along a Hilbert curve each call;
                            SPLIT for tile pairs whose bounding boxes are
-                           closer than near_gamma (default 1/64) times
-                           their largest coordinate, SINGLE for the rest   */
+                           closer than near_gamma (default 1/64; 1/256 on
+                           the batched symmetric path) times their largest
+                           coordinate, SINGLE for the rest                 */
 } nb_positions;
 
 /* How the pairs of one system (nb_forces, nb_step with B = 1) are evaluated
@@ -136,7 +137,8 @@ typedef struct nb_opts {
     int32_t positions;      /* nb_positions (ignored by NB_PREC_FP64)          */
     float near_gamma;       /* NB_POS_ADAPTIVE: a tile pair is well separated
                                when its box gap >= near_gamma x the largest
-                               coordinate magnitude; 0 = default (1/64)     */
+                               coordinate magnitude; 0 = default (1/64;
+                               1/256 on the batched symmetric path)       */
     int32_t pairs;          /* nb_pairs                                       */
 } nb_opts;
 
