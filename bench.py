@@ -189,7 +189,8 @@ def cpu_baseline(seconds: float = 10.0, gpu=None):
     rate = nrows * N_MAIN / el / 1e9
     info = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{nrows} exact rows x {N_MAIN} j of the 2^20 Plummer sphere "
-                      f"(FP64 C, OpenMP over rows), {el:.1f} s"}
+                      f"(FP64 C, OpenMP over rows), {el:.1f} s",
+            "other_sizes": _oracle_other_sizes()}
     acc = None
     if gpu:
         acc = {"rows": nrows, "reference": "the FP64 oracle's exact rows above",
@@ -197,6 +198,30 @@ def cpu_baseline(seconds: float = 10.0, gpu=None):
         for name, (a, p) in gpu.items():
             acc[name] = accuracy_on_rows(a[rows], p[rows], ra, rp)
     return info, acc
+
+
+def _oracle_other_sizes(seconds: float = 2.0):
+    """The oracle's rate on the 65536 log-normal and 16384 Plummer workloads
+    (sampled rows against all j, about `seconds` each), for comparison."""
+    import numpy as np
+
+    import oracle
+    from paper_2605_02744_gb300 import ics
+    out = {}
+    for name, s, eps in (("plummer_lognormal_65536", ics.plummer_lognormal(65536, 0), 1e-3),
+                         ("plummer_16384", ics.plummer(16384, 0), 5e-3)):
+        n = s.mass.shape[0]
+        rng = np.random.default_rng(4)
+        t0 = time.perf_counter()
+        oracle.forces_rows(s.pos, s.mass, eps, rng.choice(n, 256, replace=False))
+        dt = time.perf_counter() - t0
+        nrows = int(max(256, min(n, 256 * seconds / max(dt, 1e-3))))
+        rows = rng.choice(n, nrows, replace=False)
+        t0 = time.perf_counter()
+        oracle.forces_rows(s.pos, s.mass, eps, rows)
+        el = time.perf_counter() - t0
+        out[name] = {"value": nrows * n / el / 1e9, "unit": UNIT, "rows": nrows}
+    return out
 
 
 def accuracy_on_rows(a, p, ra, rp):
@@ -530,6 +555,8 @@ def run_ours(args):
                        "force + potential evaluation), nb_energy, pos/vel/acc/pot/energy -> "
                        "host; wall clock"},
         "gpu_launches": kahan_launches,
+        # the same rate with N (N - 1) interactions per step (no self pairs)
+        "value_counting_n_n_minus_1": value * (N_MAIN - 1) / N_MAIN,
         "variants": {"f64acc_value": ws * args.steps * inter / (sum(results["f64acc"][0]) * 1e-3)
                      / 1e9, "f64acc_ms_per_step": f64_ms,
                      "kahan_ms_per_step": step_ms,
