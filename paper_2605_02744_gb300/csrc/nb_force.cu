@@ -100,7 +100,6 @@ __device__ __forceinline__ int64_t slot_of(int64_t b, int k, int tid) {
 template <int NT, int IR, int POL, bool GUARD, bool NF>
 __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
                                                const Acc<POL> (&acc)[IR][4], const float (&mi)[IR]) {
-    constexpr int BI = NT * IR;
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
