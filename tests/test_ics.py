@@ -2,7 +2,6 @@
 import math
 
 import numpy as np
-import pytest
 from scipy import stats
 
 from paper_2605_02744_gb300 import ics

@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from paper_2605_02744_gb300 import api, binding, ics
-from tests.gpu_util import dev, host
+from tests.gpu_util import host
 
 pytestmark = pytest.mark.gpu
 

@@ -7,7 +7,6 @@ run every other test; it also passes on its own in a fresh process.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
