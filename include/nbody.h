@@ -156,6 +156,24 @@ const char *nb_last_error(void);
  * threads).  Kernels replayed from a captured CUDA graph are not counted. */
 unsigned long long nb_launch_count(void);
 
+/*
+ * Opt-in timing of the dominant kernel, the symmetric FP32-pair kernel of
+ * nb_forces / nb_step (not its fold or the O(N) kernels): while enabled, a
+ * pair of CUDA events is recorded on the launch stream just before and after
+ * each of its launches (none inside a stream capture).  enable = 1 clears
+ * the record and starts timing, 0 stops it.  Process-wide; meant for one
+ * host thread.  Always returns NB_OK.
+ */
+int nb_kernel_timing(int32_t enable);
+
+/*
+ * Waits for the launches timed since nb_kernel_timing(1) and returns their
+ * summed duration in ms and their number.  NB_ERR_INVALID for NULL
+ * pointers; NB_ERR_CUDA if an event could not be created, recorded or read
+ * (the outputs are then 0).
+ */
+int nb_kernel_time(double *total_ms, int64_t *launches);
+
 /* 1 if `tune` names a kernel shape compiled into this build (and an
  * item_blocks of 0, 2, 4 or 8), else 0. */
 int nb_tune_valid(const nb_tune *tune);

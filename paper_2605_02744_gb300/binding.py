@@ -44,7 +44,8 @@ PAIRS = {"default": NB_PAIRS_DEFAULT, "direct": NB_PAIRS_DIRECT,
 EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
-            "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4")
+            "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4",
+            "nb_kernel_timing", "nb_kernel_time")
 
 
 class NbError(RuntimeError):
@@ -93,6 +94,8 @@ _SIGS = {
     "nb_version": (ctypes.c_char_p, []),
     "nb_last_error": (ctypes.c_char_p, []),
     "nb_launch_count": (ctypes.c_ulonglong, []),
+    "nb_kernel_timing": (ctypes.c_int, [_i32]),
+    "nb_kernel_time": (ctypes.c_int, [ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "nb_tune_valid": (ctypes.c_int, [ctypes.POINTER(nb_tune)]),
     "nb_workspace_bytes": (_sz, [_i64, _i32, _OPTS]),
     "nb_forces": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _sz, _OPTS]),
@@ -185,6 +188,19 @@ def nb_last_error() -> str:
 
 def nb_launch_count() -> int:
     return int(lib().nb_launch_count())
+
+
+def nb_kernel_timing(enable: bool) -> None:
+    _check(lib().nb_kernel_timing(1 if enable else 0))
+
+
+def nb_kernel_time():
+    """(summed ms, launches) of the pair-kernel launches timed since
+    nb_kernel_timing(True)."""
+    ms = _d(0.0)
+    n = _i64(0)
+    _check(lib().nb_kernel_time(ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
 
 
 def nb_tune_valid(tune) -> bool:

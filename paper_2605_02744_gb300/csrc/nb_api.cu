@@ -37,6 +37,49 @@ int cuda_check(cudaError_t e, const char *what) {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// Kernel timer: a pool of event pairs reused from one nb_kernel_timing(1) to
+// the next; g_tm_used pairs hold a recorded launch.
+static std::mutex g_tm_mu;
+static bool g_tm_on = false, g_tm_open = false;
+static int g_tm_err = 0;
+static size_t g_tm_used = 0;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tm_ev;
+
+static bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+void kernel_timer_begin(cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (!g_tm_on || g_tm_open || g_tm_err || capturing(st)) return;
+    if (g_tm_used == g_tm_ev.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            g_tm_err = 1;
+            return;
+        }
+        g_tm_ev.push_back({a, b});
+    }
+    if (cudaEventRecord(g_tm_ev[g_tm_used].first, st) != cudaSuccess) {
+        g_tm_err = 1;
+        return;
+    }
+    g_tm_open = true;
+}
+
+void kernel_timer_end(cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (!g_tm_open) return;
+    g_tm_open = false;
+    if (cudaEventRecord(g_tm_ev[g_tm_used].second, st) != cudaSuccess) {
+        g_tm_err = 1;
+        return;
+    }
+    ++g_tm_used;
+}
+
 // ----------------------------------------------------------------- device
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -323,6 +366,38 @@ const char *nb_version(void) {
 const char *nb_last_error(void) { return g_err; }
 
 unsigned long long nb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int nb_kernel_timing(int32_t enable) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (enable) {
+        g_tm_used = 0;
+        g_tm_err = 0;
+        g_tm_open = false;
+    }
+    g_tm_on = enable != 0;
+    return NB_OK;
+}
+
+int nb_kernel_time(double *total_ms, int64_t *launches) {
+    clear_error();
+    if (!total_ms || !launches) return fail(NB_ERR_INVALID, "total_ms and launches are required");
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    *total_ms = 0.0;
+    *launches = 0;
+    if (g_tm_err) return fail(NB_ERR_CUDA, "a timing event could not be created or recorded");
+    double sum = 0.0;
+    for (size_t k = 0; k < g_tm_used; ++k) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(g_tm_ev[k].second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, g_tm_ev[k].first, g_tm_ev[k].second);
+        if (e != cudaSuccess) return cuda_check(e, "kernel timing events");
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = (int64_t)g_tm_used;
+    return NB_OK;
+}
 
 int nb_tune_valid(const nb_tune *t) {
     if (!t) return 0;

@@ -53,6 +53,11 @@ int smem_optin(const void *kernel, size_t bytes);
 // Counts kernels this library enqueued (nb_launch_count); a CUDA-graph
 // replay launches the captured kernels without passing through here.
 void count_launch(int n = 1);
+// Opt-in CUDA-event timing of the symmetric FP32 pair kernel
+// (nb_kernel_timing): events recorded on `st` just before and after its
+// launch; no-ops when timing is off or `st` is being captured.
+void kernel_timer_begin(cudaStream_t st);
+void kernel_timer_end(cudaStream_t st);
 // Resident CTAs per SM of `kernel` (>= 1), and the persistent grid size:
 // min(requested CTAs per SM, occupancy) x SMs, capped at `total` items.
 int occupancy(const void *kernel, int threads, size_t smem);

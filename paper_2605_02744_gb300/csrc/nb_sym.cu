@@ -667,7 +667,9 @@ int launch_pair(const SymParams &p, cudaStream_t st) {
                         (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
     const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
     if (rc != NB_OK) return rc;
+    kernel_timer_begin(st);
     kern<<<(unsigned)p.ctas, SNT, smem, st>>>(p);
+    kernel_timer_end(st);
     count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;

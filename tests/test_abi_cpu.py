@@ -208,3 +208,11 @@ def test_batched_item_width(B):
     d = _opts(B, pairs=B.NB_PAIRS_DIRECT, tune=ctypes.pointer(t))
     assert B.nb_workspace_bytes(n, b, d) == B.nb_workspace_bytes(
         n, b, _opts(B, pairs=B.NB_PAIRS_DIRECT))
+
+
+def test_kernel_timing_hook_without_launches(B):
+    lib = B.lib()
+    assert lib.nb_kernel_timing(1) == B.NB_OK
+    assert B.nb_kernel_time() == (0.0, 0)
+    assert lib.nb_kernel_time(None, None) == B.NB_ERR_INVALID
+    assert lib.nb_kernel_timing(0) == B.NB_OK

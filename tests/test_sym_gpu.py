@@ -172,3 +172,27 @@ def test_symmetric_fp64_step_loop():
     assert np.abs(host(g.pos) - host(b.pos)).max() <= 1e-12 * max(dx, 1.0)
     assert rel_vec_err(host(g.acc), host(b.acc)).max() <= 1e-12
     assert rel_err(host(g.pot), host(b.pot)).max() <= 1e-12
+
+
+def test_kernel_timing_hook_times_each_pair_launch():
+    # nb_kernel_timing: one event pair per symmetric pair-kernel launch, on
+    # the launch stream; the pair kernel is part of each call's time
+    s = _system(40000, 3)
+    pos, mass = dev(s.pos), dev(s.mass)
+    api.forces(pos, mass, 1e-3, precision="kahan")  # warm-up (graph of sizes, opt-ins)
+    torch.cuda.synchronize()
+    binding.nb_kernel_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        api.forces(pos, mass, 1e-3, precision="kahan")
+    e1.record()
+    torch.cuda.synchronize()
+    ms, n = binding.nb_kernel_time()
+    binding.nb_kernel_timing(False)
+    assert n == 3
+    assert 0.0 < ms <= e0.elapsed_time(e1)
+    # stopped: further launches are not recorded, and the record stays
+    api.forces(pos, mass, 1e-3, precision="kahan")
+    torch.cuda.synchronize()
+    assert binding.nb_kernel_time()[1] == 3
