@@ -287,8 +287,12 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
             // still in flight land (bounded), and leave together.
             if (tid == 0) {
                 set_status(p.status, kStatusTimeout);
+                // copies still in flight must land before the CTA exits: at least
+                // the default bound, however short the caller's limit
+                const long long drain = p.timeout > kDefaultTimeoutCycles ? p.timeout
+                                                                       : kDefaultTimeoutCycles;
                 for (int64_t r = q; r < nq && r < q + ST; ++r)
-                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), p.timeout);
+                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
             }
             __syncthreads();
             return;

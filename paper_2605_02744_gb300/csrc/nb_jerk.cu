@@ -207,8 +207,12 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 set_status(p.status, kStatusTimeout);
+                // copies still in flight must land before the CTA exits: at least
+                // the default bound, however short the caller's limit
+                const long long drain = p.timeout > kDefaultTimeoutCycles ? p.timeout
+                                                                       : kDefaultTimeoutCycles;
                 for (int64_t r = q; r < nq && r < q + ST; ++r)
-                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), p.timeout);
+                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
             }
             __syncthreads();
             return;
