@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -85,11 +86,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"nb_clocks_gpu{index}_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
@@ -110,6 +111,10 @@ class ClockSampler:
 
     def summary(self):
         if self.proc is None:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         with open(self.path) as f:
@@ -117,6 +122,10 @@ class ClockSampler:
                 p = [x.strip() for x in line.split(",")]
                 if len(p) >= 9 and p[1].replace(".", "").isdigit():
                     rows.append(p)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows]
@@ -392,10 +401,16 @@ def variant_rates(torch):
 
 
 def adjoint_ratio(torch):
-    """Forward (200 KDK steps) vs gradient time at the 16384-particle workload."""
-    from paper_2605_02744_gb300 import adjoint, ics
+    """Forward (200 KDK steps) vs gradient time at the 16384-particle workload;
+    the target is the final state of an FP64-pair run (this library) from
+    the initial positions perturbed by N(0, (1e-3)^2), seed 2."""
+    from paper_2605_02744_gb300 import adjoint, api, ics
     s = ics.plummer(16384, seed=0)
-    target = ics.perturb_positions(s.pos, 1e-3, seed=2)
+    t = api.System(ics.perturb_positions(s.pos, 1e-3, seed=2), s.vel, s.mass, 5e-3,
+                   precision="fp64")
+    t.step(1e-3, 200)
+    target = t.pos.cpu().numpy()
+    del t
     return adjoint.time_forward_backward(s, target, eps=5e-3, dt=1e-3, nsteps=200, segment=20,
                                          precision="f64acc")
 
@@ -487,7 +502,7 @@ def run_ours(args):
         st.synchronize()
 
     e2e_step()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()

@@ -160,9 +160,13 @@ unsigned long long nb_launch_count(void);
  * Opt-in timing of the dominant kernel, the symmetric FP32-pair kernel of
  * nb_forces / nb_step (not its fold or the O(N) kernels): while enabled, a
  * pair of CUDA events is recorded on the launch stream just before and after
- * each of its launches (none inside a stream capture).  enable = 1 clears
- * the record and starts timing, 0 stops it.  Process-wide; meant for one
- * host thread.  Always returns NB_OK.
+ * each of its launches (none inside a stream capture).  The events come from
+ * a ring of 64 pairs on the device that is current at nb_kernel_timing(1);
+ * when all 64 hold unread times, the next launch first waits on the host for
+ * the oldest and adds it to the running total.  Launches on another device
+ * mark the record as failed.  enable = 1 clears the record and starts
+ * timing, 0 stops it.  Process-wide; meant for one host thread.  Always
+ * returns NB_OK.
  */
 int nb_kernel_timing(int32_t enable);
 
@@ -208,17 +212,24 @@ int nb_forces(const double *pos, const double *mass, int64_t N, double eps, doub
  * synchronise the device).  The paper has no counterpart; this is a
  * convenience of this library.
  *
- * Same arguments and results as nb_forces without (ws, ws_bytes): the
+ * Same arguments and results as nb_forces without (ws, ws_bytes), on the
+ * direct kernel (every ordered pair) with one fixed launch shape: the
  * scratch is a fixed device array inside the library (about 6.2 MB, held on
  * every GPU that loads the library until the process exits), so N is limited
- * to 32768; larger N returns NB_ERR_INVALID.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress), so make the
- * first call on each device before capturing any CUDA stream.  Every call
- * shares the one array: calls that may overlap on the GPU (different
- * streams, or different host threads) race and must be serialised by the
- * caller.  Each call clears the array's counters and status word itself.
- * Device-side errors (a non-finite result, a wait that ran out) are not
- * reported by this variant; host-side argument errors are.
+ * to 32768; larger N returns NB_ERR_INVALID.  Options it does not serve are
+ * refused with NB_ERR_UNSUPPORTED: opts->pairs = NB_PAIRS_SYMMETRIC,
+ * opts->positions = NB_POS_ADAPTIVE and a non-NULL opts->tune (DEFAULT pairs
+ * mean DIRECT here; DEFAULT positions mean SPLIT for KAHAN and F64ACC and
+ * SINGLE for FP32, as in nb_forces).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress), so make the first call
+ * on each device before capturing any CUDA stream.  Every call shares the
+ * one array: calls that may overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  Each
+ * call clears the array's counters and status word itself.  Device-side
+ * errors (a non-finite result, a wait that ran out) are latched in the
+ * array's status word: nb_poll_status(NULL, 0, stream) reads and clears it
+ * for the current device, and must be called before the next call, which
+ * clears it.
  */
 int nb_forces_noalloc(const double *pos, const double *mass, int64_t N, double eps, double *acc,
                       double *pot, const nb_opts *opts);
@@ -379,8 +390,12 @@ int nb_hermite4(double *pos, double *vel, const double *mass, int64_t N, double 
 
 /*
  * Synchronises `stream`, reads the device status word latched in ws (a
- * bitwise OR of 1 << NB_ERR_TIMEOUT and 1 << NB_ERR_NONFINITE), clears it,
- * and returns the matching NB_ERR_* code (timeout first) or NB_OK.
+ * bitwise OR of 1 << NB_ERR_TIMEOUT, 1 << NB_ERR_INVALID and
+ * 1 << NB_ERR_NONFINITE), clears it, and returns the matching NB_ERR_* code
+ * (timeout first, then invalid, then non-finite) or NB_OK.  ws = NULL reads
+ * the status word of nb_forces_noalloc's fixed array on the current device
+ * (ws_bytes is then ignored).  NB_ERR_INVALID (as a host error) for a
+ * non-NULL ws of fewer than 256 bytes.
  */
 int nb_poll_status(void *ws, size_t ws_bytes, void *stream);
 

@@ -319,8 +319,11 @@ def nb_hermite4(pos, vel, mass, eps: float, acc, jerk, acc_valid: bool, dt: floa
 
 
 def nb_poll_status(ws, opts: nb_opts | None = None) -> int:
-    """Synchronises the stream and returns the latched device status code."""
+    """Synchronises the stream and returns the latched device status code;
+    ws=None polls nb_forces_noalloc's fixed array on the current device."""
     stream = opts.stream if opts is not None else None
+    if ws is None:
+        return int(lib().nb_poll_status(None, 0, stream))
     rc = lib().nb_poll_status(_dptr(ws, "ws"), ws.numel() * ws.element_size(), stream)
     return int(rc)
 

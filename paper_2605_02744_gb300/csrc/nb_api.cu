@@ -37,12 +37,19 @@ int cuda_check(cudaError_t e, const char *what) {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
-// Kernel timer: a pool of event pairs reused from one nb_kernel_timing(1) to
-// the next; g_tm_used pairs hold a recorded launch.
+// Kernel timer: a ring of at most kTimerPairs event pairs on the device that
+// was current when timing was switched on.  A launch that finds every pair
+// holding an unread measurement first folds the oldest one into g_tm_ms (an
+// event synchronisation on the host), so a long step loop reuses the same
+// few events instead of creating one pair per launch.
+constexpr size_t kTimerPairs = 64;
 static std::mutex g_tm_mu;
 static bool g_tm_on = false, g_tm_open = false;
 static int g_tm_err = 0;
-static size_t g_tm_used = 0;
+static int g_tm_dev = -1;
+static double g_tm_ms = 0.0;        // folded measurements
+static int64_t g_tm_count = 0;      // launches recorded since timing was switched on
+static size_t g_tm_head = 0, g_tm_live = 0;  // ring: oldest unread pair, unread pairs
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tm_ev;
 
 static bool capturing(cudaStream_t st) {
@@ -50,10 +57,34 @@ static bool capturing(cudaStream_t st) {
     return cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
 }
 
+// Folds the oldest unread pair into g_tm_ms (caller holds g_tm_mu).
+static int timer_fold_oldest() {
+    auto &e = g_tm_ev[g_tm_head];
+    float ms = 0.f;
+    cudaError_t r = cudaEventSynchronize(e.second);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e.first, e.second);
+    if (r != cudaSuccess) return 1;
+    g_tm_ms += ms;
+    g_tm_head = (g_tm_head + 1) % kTimerPairs;
+    --g_tm_live;
+    return 0;
+}
+
 void kernel_timer_begin(cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     if (!g_tm_on || g_tm_open || g_tm_err || capturing(st)) return;
-    if (g_tm_used == g_tm_ev.size()) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || (g_tm_dev >= 0 && dev != g_tm_dev)) {
+        g_tm_err = 1;  // events belong to one device
+        return;
+    }
+    g_tm_dev = dev;
+    if (g_tm_live == kTimerPairs && timer_fold_oldest()) {
+        g_tm_err = 1;
+        return;
+    }
+    const size_t slot = (g_tm_head + g_tm_live) % kTimerPairs;
+    while (g_tm_ev.size() <= slot) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
             if (a) cudaEventDestroy(a);
@@ -62,7 +93,7 @@ void kernel_timer_begin(cudaStream_t st) {
         }
         g_tm_ev.push_back({a, b});
     }
-    if (cudaEventRecord(g_tm_ev[g_tm_used].first, st) != cudaSuccess) {
+    if (cudaEventRecord(g_tm_ev[slot].first, st) != cudaSuccess) {
         g_tm_err = 1;
         return;
     }
@@ -73,11 +104,13 @@ void kernel_timer_end(cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     if (!g_tm_open) return;
     g_tm_open = false;
-    if (cudaEventRecord(g_tm_ev[g_tm_used].second, st) != cudaSuccess) {
+    const size_t slot = (g_tm_head + g_tm_live) % kTimerPairs;
+    if (cudaEventRecord(g_tm_ev[slot].second, st) != cudaSuccess) {
         g_tm_err = 1;
         return;
     }
-    ++g_tm_used;
+    ++g_tm_live;
+    ++g_tm_count;
 }
 
 // ----------------------------------------------------------------- device
@@ -371,7 +404,20 @@ int nb_kernel_timing(int32_t enable) {
     clear_error();
     std::lock_guard<std::mutex> lk(g_tm_mu);
     if (enable) {
-        g_tm_used = 0;
+        // events of an earlier device are released; this device's are reused
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+        if (dev != g_tm_dev && g_tm_dev >= 0) {
+            for (auto &e : g_tm_ev) {
+                cudaEventDestroy(e.first);
+                cudaEventDestroy(e.second);
+            }
+            g_tm_ev.clear();
+        }
+        g_tm_dev = dev;
+        g_tm_ms = 0.0;
+        g_tm_count = 0;
+        g_tm_head = g_tm_live = 0;
         g_tm_err = 0;
         g_tm_open = false;
     }
@@ -385,17 +431,15 @@ int nb_kernel_time(double *total_ms, int64_t *launches) {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     *total_ms = 0.0;
     *launches = 0;
-    if (g_tm_err) return fail(NB_ERR_CUDA, "a timing event could not be created or recorded");
-    double sum = 0.0;
-    for (size_t k = 0; k < g_tm_used; ++k) {
-        float ms = 0.f;
-        cudaError_t e = cudaEventSynchronize(g_tm_ev[k].second);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, g_tm_ev[k].first, g_tm_ev[k].second);
-        if (e != cudaSuccess) return cuda_check(e, "kernel timing events");
-        sum += ms;
+    if (g_tm_err) return fail(NB_ERR_CUDA, "a timing event could not be created, recorded or read");
+    while (g_tm_live > 0) {
+        if (timer_fold_oldest()) {
+            g_tm_err = 1;
+            return fail(NB_ERR_CUDA, "kernel timing events could not be read");
+        }
     }
-    *total_ms = sum;
-    *launches = (int64_t)g_tm_used;
+    *total_ms = g_tm_ms;
+    *launches = g_tm_count;
     return NB_OK;
 }
 
@@ -794,7 +838,14 @@ int nb_hermite4(double *pos, double *vel, const double *mass, int64_t N, double 
 
 int nb_poll_status(void *ws, size_t ws_bytes, void *stream) {
     clear_error();
-    if (!ws || ws_bytes < 256) return fail(NB_ERR_INVALID, "workspace NULL or too small");
+    if (!ws) {
+        // the status word of nb_forces_noalloc's fixed array on this device
+        uint32_t *word_dev = nullptr;
+        NB_TRY(noalloc_status_word(&word_dev));
+        ws = word_dev;
+    } else if (ws_bytes < 256) {
+        return fail(NB_ERR_INVALID, "workspace too small");
+    }
     NB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     uint32_t word = 0;
     NB_CUDA(cudaMemcpy(&word, ws, sizeof word, cudaMemcpyDeviceToHost));

@@ -309,4 +309,7 @@ int bsym_item_blocks(const nb_opts *opts);
 bool bsym_wanted(const nb_opts *opts, int64_t N, int32_t B);
 int launch_batched_sym(const BatchedJob &job);
 
+// Device address of nb_forces_noalloc's status word on the current device.
+int noalloc_status_word(uint32_t **out);
+
 }  // namespace nb

@@ -49,6 +49,15 @@ static int scratch_address(void **out) {
     return NB_OK;
 }
 
+// Status word of the array on the current device (nb_poll_status(NULL, ...)).
+int noalloc_status_word(uint32_t **out) {
+    void *base = nullptr;
+    const int rc = scratch_address(&base);
+    if (rc != NB_OK) return rc;
+    *out = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + kNaStatus);
+    return NB_OK;
+}
+
 }  // namespace nb
 
 using namespace nb;
@@ -72,8 +81,18 @@ extern "C" int nb_forces_noalloc(const double *pos, const double *mass, int64_t 
     if (!isfinite(o->G)) return fail(NB_ERR_INVALID, "G must be finite");
     if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
         return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
-    if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_SINGLE)
+    if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_ADAPTIVE)
         return fail(NB_ERR_INVALID, "unknown positions mode %d", o->positions);
+    if (o->pairs < NB_PAIRS_DEFAULT || o->pairs > NB_PAIRS_SYMMETRIC)
+        return fail(NB_ERR_INVALID, "unknown pairs mode %d", o->pairs);
+    // the fixed array holds the direct kernel's scratch only: no Hilbert
+    // sort buffers, no symmetric-pair sums, one compiled launch shape
+    if (o->positions == NB_POS_ADAPTIVE)
+        return fail(NB_ERR_UNSUPPORTED, "nb_forces_noalloc has no adaptive (sorted) positions");
+    if (o->pairs == NB_PAIRS_SYMMETRIC)
+        return fail(NB_ERR_UNSUPPORTED, "nb_forces_noalloc evaluates every ordered pair only");
+    if (o->tune)
+        return fail(NB_ERR_UNSUPPORTED, "nb_forces_noalloc runs one fixed launch shape");
     if ((int64_t)kNoAllocCtasPerSm * device_sm_count() > kNoAllocMaxGrid)
         return fail(NB_ERR_UNSUPPORTED, "device has more SMs than the fixed scratch serves");
 
@@ -83,7 +102,8 @@ extern "C" int nb_forces_noalloc(const double *pos, const double *mass, int64_t 
     char *ws = static_cast<char *>(base);
     cudaStream_t st = (cudaStream_t)o->stream;
     // The array keeps the previous call's contents: the status word and the
-    // arrival counters must start at zero.
+    // arrival counters must start at zero (a status the caller has not polled
+    // is lost here).
     NB_CUDA(cudaMemsetAsync(ws, 0, kNaPack, st));
 
     ForceJob j;
