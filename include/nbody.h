@@ -91,11 +91,17 @@ typedef enum {
  * applies it to both particles: the pair term of Eq. 1 changes sign under
  * i <-> j apart from the masses, so d, r^2 and r^-3 serve a_i and a_j
  * (about 9 FP32 operations per directed interaction instead of 13).  It
- * needs eps > 0 and a workspace of about N^2 / 256 bytes for the j-side
- * partial sums (4.3 GB at N = 2^20), which nb_workspace_bytes includes when
- * the path is in use.  DEFAULT takes SYMMETRIC for 32768 <= N <= 2^21 and
- * eps > 0, DIRECT otherwise; FP64 pairs (NB_PREC_FP64) keep FP64 partials,
- * twice the bytes, and DEFAULT takes them for 32768 <= N <= 2^20.  For batches (B > 1, nb_forces_batched and
+ * needs eps > 0.  The partial sums that several CTAs produce for one
+ * particle are combined in two-word fixed point with integer atomic adds
+ * (exact, so the result does not depend on their order), which takes 64 B
+ * per particle of workspace plus 12 B per pair of 2048-particle blocks
+ * (about 69 MB at N = 2^20), included by nb_workspace_bytes when the path is
+ * in use.  The fixed-point grid is 2^-100 of the a-priori bound
+ * N max|m| max(0.385 / eps^2, 1 / eps) on every acceleration component and
+ * potential; it is finer than FP64 rounding unless that bound exceeds the
+ * smallest |a_i| by more than ~10^14.  DEFAULT takes SYMMETRIC for
+ * 32768 <= N <= 2^24 and eps > 0 (FP32 and FP64 pairs), DIRECT otherwise.
+ * For batches (B > 1, nb_forces_batched and
  * nb_step with offsets) DEFAULT and SYMMETRIC take the symmetric batched
  * path (warp-granular work items; workspace about 250 B per particle plus
  * 2 KiB per pair of 128-particle blocks of a cluster: 0.9 GB for 512

@@ -65,9 +65,10 @@ def forces_host(pos, mass, eps: float, precision="f64acc", G: float = 1.0, tune=
 
 
 def forces_batched(pos, mass, offsets, eps, precision="f64acc", G: float = 1.0, ws=None,
-                   stream=None):
-    """(acc, pot) for B independent clusters described by CSR offsets."""
-    opts = B.make_opts(precision, G, stream)
+                   stream=None, pairs="default"):
+    """(acc, pot) for B independent clusters described by CSR offsets;
+    pairs: "default"/"symmetric" (symmetric batched path) or "direct"."""
+    opts = B.make_opts(precision, G, stream, pairs=pairs)
     n = mass.shape[0]
     nb = offsets.shape[0] - 1
     acc = torch.empty((n, 3), dtype=torch.float64, device=pos.device)

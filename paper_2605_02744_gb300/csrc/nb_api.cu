@@ -217,14 +217,9 @@ WsLayout ws_layout(int64_t N, int32_t B, const nb_opts *opts) {
     off = align256(off + kScratchBase + batched_scratch_bytes(B));
     if (sym_wanted(opts, N, B)) {
         const SymSizes z = sym_sizes(L.Np);
-        // FP64 pairs keep FP64 partials: twice the bytes
-        const size_t pb = z.p_bytes * (opts->precision == NB_PREC_FP64 ? 2 : 1);
-        L.sym_p = off;
-        L.sym_p_bytes = pb;
-        off = align256(off + pb);
-        L.sym_rec = off;
-        L.sym_rec_bytes = z.rec_bytes;
-        off = align256(off + z.rec_bytes);
+        L.sym_fx = off;
+        L.sym_fx_bytes = z.fx_bytes;
+        off = align256(off + z.fx_bytes);
         L.sym_cost = off;
         off = align256(off + z.cost_bytes);
     }
@@ -250,9 +245,7 @@ bool bsym_wanted(const nb_opts *o, int64_t N, int32_t B) {
 bool sym_wanted(const nb_opts *o, int64_t N, int32_t B) {
     if (!o || B != 1) return false;
     if (o->pairs == NB_PAIRS_SYMMETRIC) return true;
-    // FP64 partials are twice as large: half the range
-    const int64_t top = o->precision == NB_PREC_FP64 ? kSymMaxN / 2 : kSymMaxN;
-    return o->pairs == NB_PAIRS_DEFAULT && N >= kSymMinN && N <= top;
+    return o->pairs == NB_PAIRS_DEFAULT && N >= kSymMinN && N <= kSymMaxN;
 }
 
 int check_ws(const void *ws, size_t ws_bytes, const WsLayout &L) {

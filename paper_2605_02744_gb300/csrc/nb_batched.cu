@@ -283,7 +283,6 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
     const int lane = tid % L;
     const int grp = tid / L;
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR];
-    float mi[IR];
     int64_t sl[IR];
     Acc<POL> tot[IR][4];
     float wlo[3] = {3e38f, 3e38f, 3e38f}, whi[3] = {-3e38f, -3e38f, -3e38f};
@@ -295,7 +294,6 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
         const float x = __ldcg(pk + i), y = __ldcg(pk + p.Np + i), z = __ldcg(pk + 2 * p.Np + i);
         const float xl = __ldcg(pk + 4 * p.Np + i), yl = __ldcg(pk + 5 * p.Np + i),
                     zl = __ldcg(pk + 6 * p.Np + i);
-        mi[k] = __ldcg(pk + 3 * p.Np + i);
         if (live) {
             wlo[0] = fminf(wlo[0], x); whi[0] = fmaxf(whi[0], x);
             wlo[1] = fminf(wlo[1], y); whi[1] = fmaxf(whi[1], y);
@@ -360,12 +358,33 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
 #pragma unroll
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
         const int nquads = (nj + 3) / 4;  // a ragged tail reads the zero-mass pad
+        // a tile that holds one of this warp's i-slots has self pairs: those
+        // quads give the pair j == i a zero mass (exact j != i)
+        bool own = false;
+#pragma unroll
+        for (int k = 0; k < IR; ++k) own |= sl[k] >= t0 && sl[k] < t0 + nj;
+        const bool diag = __any_sync(0xffffffffu, own);
         auto quad = [&](int jq, bool split) {
             const float4 X = *reinterpret_cast<const float4 *>(&tile[0][4 * jq]);
             const float4 Y = *reinterpret_cast<const float4 *>(&tile[1][4 * jq]);
             const float4 Z = *reinterpret_cast<const float4 *>(&tile[2][4 * jq]);
             const float4 M = *reinterpret_cast<const float4 *>(&tile[3][4 * jq]);
-            if (split) {
+            if (diag) {
+                int kr[IR];
+#pragma unroll
+                for (int k = 0; k < IR; ++k) kr[k] = (int)(sl[k] - t0) - 4 * jq;
+                const float4 XL = *reinterpret_cast<const float4 *>(&tile[4][4 * jq]);
+                const float4 YL = *reinterpret_cast<const float4 *>(&tile[5][4 * jq]);
+                const float4 ZL = *reinterpret_cast<const float4 *>(&tile[6][4 * jq]);
+                pair2<IR, false, true, true>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y),
+                                             f2(XL.x, XL.y), f2(YL.x, YL.y), f2(ZL.x, ZL.y),
+                                             f2(M.x, M.y), e2, nx, ny, nz, nxl, nyl, nzl, ax, ay,
+                                             az, ph, kr, 0);
+                pair2<IR, false, true, true>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w),
+                                             f2(XL.z, XL.w), f2(YL.z, YL.w), f2(ZL.z, ZL.w),
+                                             f2(M.z, M.w), e2, nx, ny, nz, nxl, nyl, nzl, ax, ay,
+                                             az, ph, kr, 2);
+            } else if (split) {
                 const float4 XL = *reinterpret_cast<const float4 *>(&tile[4][4 * jq]);
                 const float4 YL = *reinterpret_cast<const float4 *>(&tile[5][4 * jq]);
                 const float4 ZL = *reinterpret_cast<const float4 *>(&tile[6][4 * jq]);
@@ -444,7 +463,7 @@ __device__ __forceinline__ void force_chunk(const BatchedParams &p, int64_t o0, 
     for (int k = 0; k < IR; ++k) {
         if (sl[k] >= a1) continue;
         const int64_t i = o0 + perm[sl[k]];
-        const double phs = v[k][3] - (double)(mi[k] * dev::rsqrt_approx(eps2));  // self pair
+        const double phs = v[k][3];
         const double a[3] = {p.G * v[k][0], p.G * v[k][1], p.G * v[k][2]};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

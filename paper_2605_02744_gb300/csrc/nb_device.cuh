@@ -37,25 +37,32 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// One potentially blocking test of phase `parity`: the thread may be
+// suspended until the phase completes, for at most about `hint_ns`
+// nanoseconds (the suspend-time hint of mbarrier.try_wait).
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return done != 0;
 }
 
 // Waits for phase `parity` of `bar` to complete, for at most `timeout`
-// SM clock cycles.  Returns false if the limit ran out.
+// SM clock cycles.  Returns false if the limit ran out.  Each try_wait may
+// suspend the thread; its hint is a quarter of the limit (in ns at ~2 GHz,
+// at most 1 ms), so a short limit is not outlived by one suspended test.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   long long timeout) {
-    if (mbar_try_wait(bar, parity)) return true;
+    const long long q = timeout / 8;
+    const uint32_t hint = (uint32_t)(q < 1 ? 1 : (q > 1000000 ? 1000000 : q));
+    if (mbar_try_wait(bar, parity, hint)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait(bar, parity, hint)) {
         if (clock64() - t0 > timeout) return false;
     }
     return true;
@@ -93,14 +100,18 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // ------------------------------------------------------------ pair loop
 // Two j-particles (packed in the .x/.y halves) against IR i-particles.
 // The displacement is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) when SPLIT.
-template <int IR, bool GUARD, bool SPLIT>
+// SELF (tiles that hold some of the i-particles): kr[k] is i-particle k's
+// offset from the tile base and jj the offset of the .x j-particle; the
+// pair j == i gets a zero mass, so Eq. 1's j != i holds exactly.
+template <int IR, bool GUARD, bool SPLIT, bool SELF = false>
 __device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const float2 zj,
                                       const float2 xl, const float2 yl, const float2 zl,
                                       const float2 mj, const float2 eps2, const float2 (&nx)[IR],
                                       const float2 (&ny)[IR], const float2 (&nz)[IR],
                                       const float2 (&nxl)[IR], const float2 (&nyl)[IR],
                                       const float2 (&nzl)[IR], float2 (&ax)[IR],
-                                      float2 (&ay)[IR], float2 (&az)[IR], float2 (&ph)[IR]) {
+                                      float2 (&ay)[IR], float2 (&az)[IR], float2 (&ph)[IR],
+                                      const int *kr = nullptr, int jj = 0) {
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
         float2 dx = add2(xj, nx[k]);
@@ -119,7 +130,12 @@ __device__ __forceinline__ void pair2(const float2 xj, const float2 yj, const fl
             ri.x = r2.x > 0.f ? ri.x : 0.f;
             ri.y = r2.y > 0.f ? ri.y : 0.f;
         }
-        const float2 s = mul2(mj, ri);
+        float2 m = mj;
+        if (SELF) {
+            m.x = kr[k] == jj ? 0.f : m.x;
+            m.y = kr[k] == jj + 1 ? 0.f : m.y;
+        }
+        const float2 s = mul2(m, ri);
         const float2 ri2 = mul2(ri, ri);
         const float2 s3 = mul2(s, ri2);
         ax[k] = fma2(s3, dx, ax[k]);

@@ -99,15 +99,14 @@ __device__ __forceinline__ int64_t slot_of(int64_t b, int k, int tid) {
 
 template <int NT, int IR, int POL, bool GUARD, bool NF>
 __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
-                                               const Acc<POL> (&acc)[IR][4], const float (&mi)[IR]) {
+                                               const Acc<POL> (&acc)[IR][4]) {
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
         const int64_t slot = slot_of<NT, IR, NF>(b, k, threadIdx.x);
         if (slot < p.N) {
             const int64_t i = NF ? (int64_t)p.perm[slot] : slot;
-            double phs = acc[k][3].value();
-            if (!GUARD) phs -= (double)(mi[k] * dev::rsqrt_approx(p.eps2));  // self pair
+            const double phs = acc[k][3].value();
             const double gx = p.G * acc[k][0].value();
             const double gy = p.G * acc[k][1].value();
             const double gz = p.G * acc[k][2].value();
@@ -129,15 +128,16 @@ __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
 
 // Staged j-particles [j0, j1) of one tile against the thread's IR
 // i-particles (two j per packed instruction); SPLIT picks the hi/lo
-// displacement.
-template <int IR, int TJ, bool GUARD, bool SPLIT>
+// displacement; SELF masks the pair j == i (kr: the i-particles' offsets
+// from the tile base).
+template <int IR, int TJ, bool GUARD, bool SPLIT, bool SELF = false>
 __device__ __forceinline__ void tile_pairs(const float *sx, const int j0, const int j1,
                                            const float2 eps2,
                                            const float2 (&nx)[IR], const float2 (&ny)[IR],
                                            const float2 (&nz)[IR], const float2 (&nxl)[IR],
                                            const float2 (&nyl)[IR], const float2 (&nzl)[IR],
                                            float2 (&ax)[IR], float2 (&ay)[IR], float2 (&az)[IR],
-                                           float2 (&ph)[IR]) {
+                                           float2 (&ph)[IR], const int *kr = nullptr) {
     using dev::f2;
     const float *sy = sx + TJ, *sz = sx + 2 * TJ, *sm = sx + 3 * TJ;
     const float *sxl = sx + 4 * TJ, *syl = sx + 5 * TJ, *szl = sx + 6 * TJ;
@@ -153,12 +153,14 @@ __device__ __forceinline__ void tile_pairs(const float *sx, const int j0, const 
             YL = *reinterpret_cast<const float4 *>(syl + jj);
             ZL = *reinterpret_cast<const float4 *>(szl + jj);
         }
-        pair2<IR, GUARD, SPLIT>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y), f2(XL.x, XL.y),
-                                f2(YL.x, YL.y), f2(ZL.x, ZL.y), f2(M.x, M.y), eps2, nx, ny, nz,
-                                nxl, nyl, nzl, ax, ay, az, ph);
-        pair2<IR, GUARD, SPLIT>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w), f2(XL.z, XL.w),
-                                f2(YL.z, YL.w), f2(ZL.z, ZL.w), f2(M.z, M.w), eps2, nx, ny, nz,
-                                nxl, nyl, nzl, ax, ay, az, ph);
+        pair2<IR, GUARD, SPLIT, SELF>(f2(X.x, X.y), f2(Y.x, Y.y), f2(Z.x, Z.y),
+                                      f2(XL.x, XL.y), f2(YL.x, YL.y), f2(ZL.x, ZL.y),
+                                      f2(M.x, M.y), eps2, nx, ny, nz, nxl, nyl, nzl, ax, ay, az,
+                                      ph, kr, jj);
+        pair2<IR, GUARD, SPLIT, SELF>(f2(X.z, X.w), f2(Y.z, Y.w), f2(Z.z, Z.w),
+                                      f2(XL.z, XL.w), f2(YL.z, YL.w), f2(ZL.z, ZL.w),
+                                      f2(M.z, M.w), eps2, nx, ny, nz, nxl, nyl, nzl, ax, ay, az,
+                                      ph, kr, jj + 2);
     }
 }
 
@@ -213,7 +215,6 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
     }
 
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR];
-    float mi[IR];
     float bb[8];
     Acc<POL> acc[IR][4];
     const float2 eps2 = f2(p.eps2, p.eps2);
@@ -235,7 +236,6 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
             for (int k = 0; k < IR; ++k) {
                 const int64_t i = slot_of<NT, IR, NF>(b, k, tid);
                 const float x = p.soa[i], y = p.soa[p.Np + i], z = p.soa[2 * p.Np + i];
-                mi[k] = p.soa[3 * p.Np + i];
                 nx[k] = f2(-x, -x);
                 ny[k] = f2(-y, -y);
                 nz[k] = f2(-z, -z);
@@ -258,7 +258,16 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         float2 ax[IR], ay[IR], az[IR], ph[IR];
 #pragma unroll
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
-        if (NF) {
+        // a tile that holds some of block b's slots has the self pairs: they
+        // take the masked loop (exact j != i); every other tile the plain one
+        const bool diag = jt * TJ < (b + 1) * BI && (jt + 1) * TJ > b * BI;
+        if (diag) {
+            int kr[IR];
+#pragma unroll
+            for (int k = 0; k < IR; ++k) kr[k] = (int)(slot_of<NT, IR, NF>(b, k, tid) - jt * TJ);
+            tile_pairs<IR, TJ, GUARD, SPLIT, true>(sx, 0, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, ax,
+                                                   ay, az, ph, kr);
+        } else if (NF) {
             // per (warp, 64-particle sub-tile): warp-uniform choice
 #pragma unroll 1
             for (int c = 0; c < TJ / 64; ++c) {
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         if (jt == p.ntiles - 1 || q == nq - 1) {
             // end of this CTA's segment of i-block b: tiles [seg_begin, jt]
             if (seg_begin == 0 && jt == p.ntiles - 1) {
-                force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc, mi);
+                force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc);
             } else {
                 const int slot = (b == first_block) ? 0 : 1;
                 Record *rec = p.records + (2 * c + slot) * BI;
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
 #pragma unroll
                         for (int k = 0; k < IR; ++k) merge_record<POL>(acc[k], r + k * NT + tid);
                     }
-                    force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc, mi);
+                    force_epilogue<NT, IR, POL, GUARD, NF>(p, b, acc);
                     if (tid == 0) p.counters[b] = 0u;
                 }
             }

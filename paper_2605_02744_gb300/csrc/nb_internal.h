@@ -74,11 +74,10 @@ struct WsLayout {
     size_t sortbuf;   // Hilbert keys, permutation, tile/block boxes (adaptive path)
     size_t records;   // stream-K partial records
     size_t scratch;   // O(N) reduction scratch (energy partials, batched queue)
-    size_t sym_p;     // symmetric-pair path: FP32 j-side partials per block pair
-    size_t sym_rec;   // symmetric-pair path: FP64 i-side records per row segment
-    size_t sym_cost;  // symmetric-pair path: item costs, their prefix, CTA ranges
+    size_t sym_fx;    // symmetric-pair path: fixed-point totals, 64 B per slot
+    size_t sym_cost;  // symmetric-pair path: exponent, item costs, their prefix, CTA ranges
     size_t bsym, bsym_bytes;  // batched symmetric-pair path (0 bytes: not provisioned)
-    size_t sym_p_bytes, sym_rec_bytes;  // 0 when the path is not provisioned
+    size_t sym_fx_bytes;      // 0 when the symmetric path is not provisioned
     size_t total;
     int64_t Np;       // padded particle count of the pack arrays
     int64_t max_blocks;
@@ -193,15 +192,25 @@ int launch_force(const ForceJob &job);
 // ------------------------------------------------- symmetric-pair path
 // Row blocks of 2048 slots; items are the block pairs (I, J >= I).
 constexpr int64_t kSymBlock = 2048;
-// Default size range of the symmetric-pair path (the j-side partials take
-// nb (nb - 1) / 2 x 32 KiB, nb = N / 2048: 4.3 GB at N = 2^20).
+// Default size range of the symmetric-pair path (its scratch is O(N): 64 B
+// per particle of fixed-point totals plus 12 B per block pair of cost
+// estimates, 25 MB at N = 2^22, 400 MB at 2^24).
 constexpr int64_t kSymMinN = 1 << 15;
-constexpr int64_t kSymMaxN = 1 << 21;
+constexpr int64_t kSymMaxN = 1 << 24;
 struct SymSizes {
-    int64_t nb, T, U, ctas, K;  // row blocks, items, stream-K units, CTAs, records per row
-    size_t p_bytes, rec_bytes, cost_bytes;
+    int64_t nb, T, U, ctas;  // row blocks, items, stream-K units, CTAs
+    size_t fx_bytes, cost_bytes;
 };
 SymSizes sym_sizes(int64_t Np);
+// Pointers into the symmetric path's workspace regions.
+struct SymLayout {
+    int *fx_exp;                   // fixed-point exponent of the call
+    uint32_t *cost;                // per item
+    unsigned long long *prefix;    // [T + 1]
+    int64_t *lo;                   // [ctas + 1] stream-K range starts
+    unsigned long long *acc_fx;    // [4][2][Np]
+};
+SymLayout sym_layout(char *ws, const WsLayout &L);
 // Whether the symmetric-pair path is provisioned / taken for N particles in
 // B clusters under opts (nb_pairs; FP32-pair policies, single systems).
 bool sym_wanted(const nb_opts *opts, int64_t N, int32_t B);

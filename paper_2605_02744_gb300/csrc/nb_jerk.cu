@@ -78,13 +78,16 @@ __global__ void hermite_predict_pack_kernel(const double *__restrict__ pos,
     }
 }
 
-template <int IR, bool GUARD>
+// SELF (a tile that holds some of the i-particles): kr[k] is i-particle k's
+// offset from the tile base; the pair j == i gets a zero mass (exact j != i).
+template <int IR, bool GUARD, bool SELF = false>
 __device__ __forceinline__ void jerk_pair2(const float *st, int jj, int TJ, const float2 eps2,
                                            const float2 (&nx)[IR], const float2 (&ny)[IR],
                                            const float2 (&nz)[IR], const float2 (&nxl)[IR],
                                            const float2 (&nyl)[IR], const float2 (&nzl)[IR],
                                            const float2 (&nvx)[IR], const float2 (&nvy)[IR],
-                                           const float2 (&nvz)[IR], float2 (&S)[IR][7]) {
+                                           const float2 (&nvz)[IR], float2 (&S)[IR][7],
+                                           const int *kr = nullptr) {
     using namespace dev;
     const float2 xj = *reinterpret_cast<const float2 *>(st + jj);
     const float2 yj = *reinterpret_cast<const float2 *>(st + TJ + jj);
@@ -112,7 +115,12 @@ __device__ __forceinline__ void jerk_pair2(const float *st, int jj, int TJ, cons
             ri.x = r2.x > 0.f ? ri.x : 0.f;
             ri.y = r2.y > 0.f ? ri.y : 0.f;
         }
-        const float2 s = mul2(mj, ri);
+        float2 m = mj;
+        if (SELF) {
+            m.x = kr[k] == jj ? 0.f : m.x;
+            m.y = kr[k] == jj + 1 ? 0.f : m.y;
+        }
+        const float2 s = mul2(m, ri);
         const float2 ri2 = mul2(ri, ri);
         const float2 t = mul2(s, ri2);  // m r^3
         float2 dw = mul2(dx, wx);
@@ -162,7 +170,6 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
         for (int64_t q = 0; q < nq && q < ST; ++q) issue(q);
 
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR], nvx[IR], nvy[IR], nvz[IR];
-    float mi[IR];
     Acc<POL> T[IR][7];
     const float2 eps2 = f2(p.eps2, p.eps2);
     for (int64_t q = 0; q < nq; ++q) {
@@ -175,7 +182,6 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
                 float v[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) v[c] = p.soa[c * p.Np + i];
-                mi[k] = v[3];
                 nx[k] = f2(-v[0], -v[0]);
                 ny[k] = f2(-v[1], -v[1]);
                 nz[k] = f2(-v[2], -v[2]);
@@ -197,9 +203,21 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
         for (int k = 0; k < IR; ++k)
 #pragma unroll
             for (int e = 0; e < 7; ++e) S[k][e] = f2(0.f, 0.f);
+        if (jt * TJ < (b + 1) * BI && (jt + 1) * TJ > b * BI) {
+            // the tile holds some of block b's particles: mask the self pairs
+            int kr[IR];
+#pragma unroll
+            for (int k = 0; k < IR; ++k) kr[k] = (int)(b * BI + k * NT + tid - jt * TJ);
 #pragma unroll 2
-        for (int jj = 0; jj < TJ; jj += 2)
-            jerk_pair2<IR, GUARD>(st, jj, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, nvx, nvy, nvz, S);
+            for (int jj = 0; jj < TJ; jj += 2)
+                jerk_pair2<IR, GUARD, true>(st, jj, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, nvx, nvy,
+                                            nvz, S, kr);
+        } else {
+#pragma unroll 2
+            for (int jj = 0; jj < TJ; jj += 2)
+                jerk_pair2<IR, GUARD>(st, jj, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, nvx, nvy, nvz,
+                                      S);
+        }
 #pragma unroll
         for (int k = 0; k < IR; ++k)
 #pragma unroll
@@ -227,8 +245,7 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
             for (int k = 0; k < IR; ++k) {
                 const int64_t i = b * BI + k * NT + tid;
                 if (i >= p.N) continue;
-                double phs = T[k][6].value();
-                if (!GUARD) phs -= (double)(mi[k] * rsqrt_approx(p.eps2));  // self pair
+                const double phs = T[k][6].value();
                 double a1[3], j1[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {

@@ -25,8 +25,8 @@
 //
 //   * Off-diagonal items (I < J): both halves of every pair.  The 16 warps'
 //     j-side sums of 4 j-sets are added in warp order in shared memory (one
-//     barrier per 4 j-sets) and stored as the FP32 partial P[I, J] of the
-//     J-block particles.
+//     barrier per 4 j-sets), giving the FP32 partial of the J-block
+//     particles from block I.
 //   * Diagonal items (I = J): the i-side only, over all ordered pairs of
 //     the block; the self pair (j-set 4w + k at rotation step 0 for lane
 //     slot k of warp w) gets a zero mass, so Eq. 1's j != i holds exactly.
@@ -35,16 +35,24 @@
 // (FP32, Kahan or FP64; totals kept in shared memory) every 4 j-sets (128
 // terms per running sum; for F64ACC through an FP32 middle sum in shared
 // memory that goes into FP64 every 16 j-sets, FP64 adds being slow on this
-// part), and stored once per row segment as an FP64 record.  In
-// Hilbert order a particle's strongest, mutually cancelling terms (its
-// spatial neighbours) arrive together; with 16 j-sets per flush the FP32
-// running sums of central particles of a log-normal Plummer sphere
-// (N = 300001, eps = 1e-3) lost up to 1e-5 of |a|, with 4 they stay at the
-// 2e-6 of the unsorted order.  A second kernel adds, slot by
-// slot in a fixed order, the records of the row's CTAs and the partials
-// P[I', I] for I' < I, applies G, scatters through the Hilbert permutation
-// and optionally kicks the velocity.  Every
-// sum runs in a fixed order: results are bitwise reproducible.
+// part) over the CTA's segment of a row.  In Hilbert order a particle's
+// strongest, mutually cancelling terms (its spatial neighbours) arrive
+// together; with 16 j-sets per flush the FP32 running sums of central
+// particles of a log-normal Plummer sphere (N = 300001, eps = 1e-3) lost up
+// to 1e-5 of |a|, with 4 they stay at the 2e-6 of the unsorted order.
+//
+// Combining across CTAs.  Every particle's sum collects one j-side FP32
+// partial per block above it and one i-side total per CTA that worked on its
+// row.  Both go, as they are produced, into two-word fixed-point
+// accumulators (nb_fixed.cuh) with integer atomic adds: exact and
+// independent of arrival order, so results are bitwise reproducible, and the
+// scratch is O(N) (64 B per particle) -- not a partial per block pair.  A
+// one-block kernel picks the fixed-point exponent from the a-priori bound
+// N max|m| max(0.385 / eps^2, 1 / eps) on every partial and total (the
+// largest value of |d| (|d|^2 + eps^2)^-3/2 is 0.385 / eps^2 at
+// |d| = eps / sqrt 2).  The fold kernel reads each particle's accumulators
+// once (and zeroes them for the next call), applies G, scatters through the
+// Hilbert permutation and optionally kicks the velocity.
 //
 // Displacements: single floats, hi/lo pairs (x_j.hi - x_i.hi) +
 // (x_j.lo - x_i.lo), or adaptive: per (warp i-set, j-set) the hi/lo form
@@ -56,6 +64,7 @@
 #include <cmath>
 
 #include "nb_device.cuh"
+#include "nb_fixed.cuh"
 #include "nb_internal.h"
 #include "nb_sym_core.cuh"
 
@@ -71,6 +80,12 @@ using dev::rsqrt_approx;
 namespace {
 
 using namespace symcore;
+
+#define NB_TRY_SYM(...)                \
+    do {                               \
+        const int rc_ = (__VA_ARGS__); \
+        if (rc_ != NB_OK) return rc_;  \
+    } while (0)
 
 constexpr int SW = 16;              // warps per CTA of the pair kernel
 constexpr int SNT = SW * 32;        // threads per CTA
@@ -92,42 +107,36 @@ struct SymParams {
     int64_t T;          // items nb (nb + 1) / 2
     int64_t U;          // stream-K units T * US (KB j-sets of one item each)
     int64_t ctas;       // grid size of the pair kernel
-    int64_t K;          // record slots per row
     float eps2;
     float gamma;        // adaptive threshold; the mode decides whether it is used
     const float *jbox;  // per 32 slots: lo[3], hi[3], max|x|, pad
     const float *wbox;  // per 128 slots
-    float *P;           // [nb (nb - 1) / 2][BI][4]
-    double *rec;        // [nb][K][BI][4]
+    unsigned long long *acc_fx;  // [4 components][2 words][Np] fixed-point totals
+    const int *fx_exp;           // the call's fixed-point exponent F
     const int64_t *lo;  // [ctas + 1]: CTA c owns units [lo[c], lo[c + 1])
     uint32_t *status;
 };
 
 // FP64 pairs: the common layout plus positions [N][3] and masses in
-// particle order and FP64 partials.
+// particle order.
 struct SymParams64 : SymParams {
     const double *pos64, *mass64;
     int64_t N;
     double eps2_64;
-    double *P64;        // [nb (nb - 1) / 2][BI][4]
 };
 
 __host__ __device__ inline int64_t row_start(int64_t I, int64_t nb) {
     return I * nb - I * (I - 1) / 2;
 }
 
-// The CTA whose unit range holds unit u: the last c with lo[c] <= u (the
-// ranges are contiguous and ordered; empty ranges are never the answer).
-__device__ __forceinline__ int64_t range_owner(const int64_t *lo, int64_t ctas, int64_t u) {
-    int64_t a = 0, b = ctas - 1;
-    while (a < b) {
-        const int64_t m = (a + b + 1) / 2;
-        if (__ldg(lo + m) <= u)
-            a = m;
-        else
-            b = m - 1;
-    }
-    return a;
+// Adds v to component e of slot s's fixed-point total.
+__device__ __forceinline__ void add_fixed(const SymParams &p, int e, int64_t s, double v, int F) {
+    unsigned long long *w = p.acc_fx + (int64_t)(2 * e) * p.Np + s;
+    if (!fx::add(w, w + p.Np, v, F)) dev::set_status(p.status, kStatusNonFinite);
+}
+__device__ __forceinline__ void add_fixed(const SymParams &p, int e, int64_t s, float v, int F) {
+    unsigned long long *w = p.acc_fx + (int64_t)(2 * e) * p.Np + s;
+    if (!fx::add_f32(w, w + p.Np, v, F)) dev::set_status(p.status, kStatusNonFinite);
 }
 
 __device__ __forceinline__ void load_j(const SymParams &p, int64_t s, float (&j)[7]) {
@@ -149,6 +158,7 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
     int64_t u = __ldg(p.lo + c);
     const int64_t u_end = __ldg(p.lo + c + 1);
     if (u >= u_end) return;
+    const int F = __ldg(p.fx_exp);
     const int64_t t0 = u / US;
     int64_t I = 0;
     while (row_start(I + 1, p.nb) <= t0) ++I;
@@ -205,7 +215,6 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
                 near |= (unsigned long long)m << (32 * h);
             }
         }
-        const int64_t pidx = J * (J - 1) / 2 + I;
         float jn[7];
         load_j(p, jb + qa * JS + l, jn);
         for (int q = qa; q < qb; ++q) {
@@ -256,30 +265,20 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
                     float s = 0.f;
 #pragma unroll
                     for (int w2 = 0; w2 < SW; ++w2) s += r[w2 * 32 * 4];
-                    // streaming store: the partials are read once, by the fold, and
-                    // must not evict the packed positions every CTA re-reads from L2
-                    __stcs(p.P + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, s);
+                    if (POT || e < 3) add_fixed(p, e, jb + (q + 1 - KB + qq) * JS + ll, s, F);
                 }
                 half ^= 1;
             }
         }
         u = seg_end;
         if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
-            // row segment done: FP64 record of the policy totals
-            const int64_t k = c - range_owner(p.lo, p.ctas, row_start(I, p.nb) * US);
-            // k < K by the bound of sym_sizes; never write past it
-            if (k >= p.K && tid == 0) dev::set_status(p.status, kStatusInvalid);
+            // row segment done: the policy totals into the fixed-point sums
 #pragma unroll
             for (int kk = 0; kk < IR; ++kk) {
-                if (k >= p.K) break;
-                const int64_t slot = w * 128 + 32 * kk + l;
-                double *r = p.rec + (((I * p.K + k) * BI) + slot) * 4;
-                __stcs(reinterpret_cast<double2 *>(r),
-                       make_double2(tot[(kk * 4 + 0) * SNT + tid].value(),
-                                    tot[(kk * 4 + 1) * SNT + tid].value()));
-                __stcs(reinterpret_cast<double2 *>(r) + 1,
-                       make_double2(tot[(kk * 4 + 2) * SNT + tid].value(),
-                                    tot[(kk * 4 + 3) * SNT + tid].value()));
+                const int64_t slot = I * BI + w * 128 + 32 * kk + l;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (POT || e < 3) add_fixed(p, e, slot, tot[(kk * 4 + e) * SNT + tid].value(), F);
             }
             row_open = false;
         }
@@ -290,37 +289,31 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
     }
 }
 
-template <int POL>
+// Reads and zeroes every slot's fixed-point totals (padding slots too: they
+// collect j-side sums as zero-mass test particles); for real particles,
+// applies G, writes acc / pot through the permutation (NULL = identity) and
+// optionally kicks the velocity.
 __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_t N,
                                                        const int *__restrict__ perm, double G,
                                                        double *__restrict__ acc,
                                                        double *__restrict__ pot,
-                                                       double *__restrict__ vel, double kick,
-                                                       uint32_t *status) {
+                                                       double *__restrict__ vel, double kick) {
+    const int F = __ldg(p.fx_exp);
     uint32_t bad = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.Np;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t I = s / BI, r = s % BI;
-        Acc<POL> a[4];
+        double a[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) a[e].zero();
-        const int64_t rs = row_start(I, p.nb);
-        const int64_t c0 = range_owner(p.lo, p.ctas, rs * US);
-        const int64_t c1 = range_owner(p.lo, p.ctas, (rs + (p.nb - I)) * US - 1);
-        for (int64_t k = 0; k <= c1 - c0 && k < p.K; ++k) {
-            if (__ldg(p.lo + c0 + k) == __ldg(p.lo + c0 + k + 1)) continue;  // empty range
-            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + (((I * p.K + k) * BI) + r) * 4);
-            const double2 u = __ldg(rr), v = __ldg(rr + 1);
-            add_record<POL>(a[0], u.x);
-            add_record<POL>(a[1], u.y);
-            add_record<POL>(a[2], v.x);
-            add_record<POL>(a[3], v.y);
+        for (int e = 0; e < 4; ++e) {
+            unsigned long long *wd = p.acc_fx + (int64_t)(2 * e) * p.Np + s;
+            const unsigned long long hi = __ldcs(wd), lo = __ldcs(wd + p.Np);
+            if (hi) wd[0] = 0ull;
+            if (lo) wd[p.Np] = 0ull;
+            a[e] = fx::value(hi, lo, F);
         }
-        add_partials<POL>(a, reinterpret_cast<const float4 *>(p.P) + (I * (I - 1) / 2) * BI + r, I,
-                          BI);
-        const double ph = a[3].value();
-        const double ax = G * a[0].value(), ay = G * a[1].value(), az = G * a[2].value();
-        const double gp = -G * ph;
+        if (s >= N) continue;
+        const double ax = G * a[0], ay = G * a[1], az = G * a[2];
+        const double gp = -G * a[3];
         const int64_t i = perm ? (int64_t)perm[s] : s;
         acc[3 * i] = ax;
         acc[3 * i + 1] = ay;
@@ -333,7 +326,31 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
         if (pot) pot[i] = gp;
         if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
     }
-    if (bad) dev::set_status(status, kStatusNonFinite);
+    if (bad) dev::set_status(p.status, kStatusNonFinite);
+}
+
+// The call's fixed-point exponent from the bound N max|m| max(0.385 / eps^2,
+// 1 / eps) (x 1.02 for the rounding of FP32 partial sums) on every partial
+// and total.  One block; the maximum is exact, so F is reproducible.
+__global__ void __launch_bounds__(1024) sym_exponent_kernel(const double *__restrict__ mass,
+                                                            int64_t N, double eps,
+                                                            int *__restrict__ F) {
+    __shared__ double part[32];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(mass[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = part[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            const double per = fmax(0.3849002 / (eps * eps), 1.0 / eps);
+            *F = fx::exponent_for(1.02 * (double)N * m * per);
+        }
+    }
 }
 
 // ------------------------------------------------------------- FP64 pairs
@@ -431,6 +448,7 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64
     int64_t u = __ldg(p.lo + c);
     const int64_t u_end = __ldg(p.lo + c + 1);
     if (u >= u_end) return;
+    const int F = __ldg(p.fx_exp);
     const int64_t t0 = u / US;
     int64_t I = 0;
     while (row_start(I + 1, p.nb) <= t0) ++I;
@@ -459,7 +477,6 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64
         }
         const bool sym = J != I;
         const int64_t jb = J * BI;
-        const int64_t pidx = J * (J - 1) / 2 + I;
         double jn[4];
         load_j64(p, jb + qa * JS + l, jn);
         for (int q = qa; q < qb; ++q) {
@@ -481,21 +498,20 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64
                     double sum = 0.0;
 #pragma unroll
                     for (int w2 = 0; w2 < SW; ++w2) sum += r[w2 * 32 * 4];
-                    __stcs(p.P64 + ((pidx * BI) + (q + 1 - KB + qq) * JS + ll) * 4 + e, sum);
+                    if (POT || e < 3) add_fixed(p, e, jb + (q + 1 - KB + qq) * JS + ll, sum, F);
                 }
                 half ^= 1;
             }
         }
         u = seg_end;
         if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
-            const int64_t k = c - range_owner(p.lo, p.ctas, row_start(I, p.nb) * US);
-            if (k >= p.K && tid == 0) dev::set_status(p.status, kStatusInvalid);
 #pragma unroll
             for (int kk = 0; kk < IR; ++kk) {
-                if (k >= p.K) break;
-                double *r = p.rec + (((I * p.K + k) * BI) + w * 128 + 32 * kk + l) * 4;
-                __stcs(reinterpret_cast<double2 *>(r), make_double2(S.ax[kk], S.ay[kk]));
-                __stcs(reinterpret_cast<double2 *>(r) + 1, make_double2(S.az[kk], S.ph[kk]));
+                const int64_t slot = I * BI + w * 128 + 32 * kk + l;
+                add_fixed(p, 0, slot, S.ax[kk], F);
+                add_fixed(p, 1, slot, S.ay[kk], F);
+                add_fixed(p, 2, slot, S.az[kk], F);
+                if (POT) add_fixed(p, 3, slot, S.ph[kk], F);
             }
             row_open = false;
         }
@@ -506,51 +522,6 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64
     }
 }
 
-__global__ void __launch_bounds__(256) sym_fold64_kernel(const SymParams64 p, double G,
-                                                         double *__restrict__ acc,
-                                                         double *__restrict__ pot,
-                                                         double *__restrict__ vel, double kick,
-                                                         uint32_t *status) {
-    uint32_t bad = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.N;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t I = s / BI, r = s % BI;
-        double a[4] = {0.0, 0.0, 0.0, 0.0};
-        const int64_t rs = row_start(I, p.nb);
-        const int64_t c0 = range_owner(p.lo, p.ctas, rs * US);
-        const int64_t c1 = range_owner(p.lo, p.ctas, (rs + (p.nb - I)) * US - 1);
-        for (int64_t k = 0; k <= c1 - c0 && k < p.K; ++k) {
-            if (__ldg(p.lo + c0 + k) == __ldg(p.lo + c0 + k + 1)) continue;  // empty range
-            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + (((I * p.K + k) * BI) + r) * 4);
-            const double2 u = __ldg(rr), v = __ldg(rr + 1);
-            a[0] += u.x;
-            a[1] += u.y;
-            a[2] += v.x;
-            a[3] += v.y;
-        }
-        const D4 *P4 = reinterpret_cast<const D4 *>(p.P64) + (I * (I - 1) / 2) * BI + r;
-        for (int64_t i2 = 0; i2 < I; ++i2) {
-            const D4 v = P4[i2 * BI];
-            a[0] += v.x;
-            a[1] += v.y;
-            a[2] += v.z;
-            a[3] += v.w;
-        }
-        const double ax = G * a[0], ay = G * a[1], az = G * a[2], gp = -G * a[3];
-        acc[3 * s] = ax;
-        acc[3 * s + 1] = ay;
-        acc[3 * s + 2] = az;
-        if (vel) {
-            vel[3 * s] += kick * ax;
-            vel[3 * s + 1] += kick * ay;
-            vel[3 * s + 2] += kick * az;
-        }
-        if (pot) pot[s] = gp;
-        if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
-    }
-    if (bad) dev::set_status(status, kStatusNonFinite);
-}
-
 // ------------------------------------------------ cost-weighted stream-K
 // Relative cost of one (warp, j-set) of an item.  Far pairs: the FP32 pipe
 // cycles per lane and step (off-diagonal 18, diagonal i-side only 13).  Near
@@ -559,8 +530,6 @@ __global__ void __launch_bounds__(256) sym_fold64_kernel(const SymParams64 p, do
 // of a 2^20 Plummer evaluation end within 1 % of each other (24 / 19: the
 // last CTA 3.5 % after the median).
 constexpr uint32_t kCostSymFar = 18, kCostSymNear = 36, kCostDiagFar = 13, kCostDiagNear = 28;
-constexpr uint32_t kUnitCostMin = KB * SW * kCostDiagFar;
-constexpr uint32_t kUnitCostMax = KB * SW * kCostSymNear;
 
 __device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64_t &J) {
     const double b = 2.0 * (double)nb + 1.0;
@@ -675,29 +644,35 @@ int launch_pair(const SymParams &p, cudaStream_t st) {
     return NB_OK;
 }
 
-template <int POL, int MODE>
-int launch_sym_mode(const SymParams &p, const ForceJob &j, const int *perm, uint32_t *status) {
-    {
-        uint32_t *cost = reinterpret_cast<uint32_t *>(j.ws + j.L.sym_cost);
-        unsigned long long *prefix = reinterpret_cast<unsigned long long *>(
-            j.ws + j.L.sym_cost + align_up(4 * (size_t)p.T, 256));
-        int64_t *lo = const_cast<int64_t *>(p.lo);
-        sym_cost_kernel<MODE><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, cost);
-        sym_scan_kernel<<<1, 1024, 0, j.stream>>>(cost, p.T, prefix);
-        sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(cost, prefix, p.T,
-                                                                                 p.ctas, lo);
-        count_launch(3);
-        NB_CUDA(cudaGetLastError());
-    }
-    const int rc_pair = j.pot ? launch_pair<POL, MODE, true>(p, j.stream)
-                              : launch_pair<POL, MODE, false>(p, j.stream);
-    if (rc_pair != NB_OK) return rc_pair;
-    const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
-    sym_fold_kernel<POL><<<(unsigned)fold_blocks, 256, 0, j.stream>>>(
-        p, j.N, perm, j.G, j.acc, j.pot, j.vel, j.kick, status);
+// Cost-weighted stream-K split of the items over the CTAs and the call's
+// fixed-point exponent: the kernels that run before the pair kernel.
+template <int MODE>
+int launch_split(const SymParams &p, const ForceJob &j, const SymLayout &y) {
+    sym_cost_kernel<MODE><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
+    sym_scan_kernel<<<1, 1024, 0, j.stream>>>(y.cost, p.T, y.prefix);
+    sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
+        y.cost, y.prefix, p.T, p.ctas, y.lo);
+    sym_exponent_kernel<<<1, 1024, 0, j.stream>>>(j.mass, j.N, j.eps, y.fx_exp);
+    count_launch(4);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+int launch_fold(const SymParams &p, const ForceJob &j, const int *perm) {
+    const int64_t fold_blocks = std::min<int64_t>(cdiv(p.Np, 256), 64 * (int64_t)device_sm_count());
+    sym_fold_kernel<<<(unsigned)fold_blocks, 256, 0, j.stream>>>(p, j.N, perm, j.G, j.acc, j.pot,
+                                                                 j.vel, j.kick);
     count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
+}
+
+template <int POL, int MODE>
+int launch_sym_mode(const SymParams &p, const ForceJob &j, const SymLayout &y, const int *perm) {
+    NB_TRY_SYM(launch_split<MODE>(p, j, y));
+    NB_TRY_SYM(j.pot ? launch_pair<POL, MODE, true>(p, j.stream)
+                     : launch_pair<POL, MODE, false>(p, j.stream));
+    return launch_fold(p, j, perm);
 }
 
 template <bool POT>
@@ -711,34 +686,19 @@ int launch_pair64(const SymParams64 &p, cudaStream_t st) {
     return NB_OK;
 }
 
-int launch_sym64(const SymParams64 &p, const ForceJob &j, uint32_t *status) {
-    uint32_t *cost = reinterpret_cast<uint32_t *>(j.ws + j.L.sym_cost);
-    unsigned long long *prefix = reinterpret_cast<unsigned long long *>(
-        j.ws + j.L.sym_cost + align_up(4 * (size_t)p.T, 256));
-    int64_t *lo = const_cast<int64_t *>(p.lo);
-    sym_cost_kernel<0><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, cost);
-    sym_scan_kernel<<<1, 1024, 0, j.stream>>>(cost, p.T, prefix);
-    sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(cost, prefix, p.T,
-                                                                             p.ctas, lo);
-    count_launch(3);
-    NB_CUDA(cudaGetLastError());
-    const int rc = j.pot ? launch_pair64<true>(p, j.stream) : launch_pair64<false>(p, j.stream);
-    if (rc != NB_OK) return rc;
-    const int64_t fold_blocks = std::min<int64_t>(cdiv(j.N, 256), 64 * (int64_t)device_sm_count());
-    sym_fold64_kernel<<<(unsigned)fold_blocks, 256, 0, j.stream>>>(p, j.G, j.acc, j.pot, j.vel,
-                                                                   j.kick, status);
-    count_launch();
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
+int launch_sym64(const SymParams64 &p, const ForceJob &j, const SymLayout &y) {
+    NB_TRY_SYM(launch_split<0>(p, j, y));
+    NB_TRY_SYM(j.pot ? launch_pair64<true>(p, j.stream) : launch_pair64<false>(p, j.stream));
+    return launch_fold(p, j, nullptr);
 }
 
 template <int POL>
-int launch_sym_pol(const SymParams &p, const ForceJob &j, int mode, const int *perm,
-                   uint32_t *status) {
+int launch_sym_pol(const SymParams &p, const ForceJob &j, const SymLayout &y, int mode,
+                   const int *perm) {
     switch (mode) {
-        case 0: return launch_sym_mode<POL, 0>(p, j, perm, status);
-        case 1: return launch_sym_mode<POL, 1>(p, j, perm, status);
-        default: return launch_sym_mode<POL, 2>(p, j, perm, status);
+        case 0: return launch_sym_mode<POL, 0>(p, j, y, perm);
+        case 1: return launch_sym_mode<POL, 1>(p, j, y, perm);
+        default: return launch_sym_mode<POL, 2>(p, j, y, perm);
     }
 }
 
@@ -750,49 +710,49 @@ SymSizes sym_sizes(int64_t Np) {
     z.T = z.nb * (z.nb + 1) / 2;
     z.U = z.T * US;
     z.ctas = std::min<int64_t>(CPS * (int64_t)device_sm_count(), z.U);
-    // Records per row: a cost-balanced range holds at least
-    // (U / ctas) * (min unit cost / max unit cost) - 2 units, so a row of
-    // nb * US units meets at most that many ranges plus 2; with short ranges
-    // (empty ones possible) every CTA gets a slot.
-    const double min_len =
-        (double)z.U / (double)z.ctas * (double)kUnitCostMin / (double)kUnitCostMax - 2.0;
-    int64_t K = z.ctas;
-    if (min_len >= 1.0)
-        K = std::min<int64_t>(z.ctas, (int64_t)std::ceil((double)(z.nb * US) / min_len) + 2);
-    z.K = K;
-    z.p_bytes = (size_t)(z.nb * (z.nb - 1) / 2) * kSymBlock * 16;
-    z.rec_bytes = (size_t)z.nb * (size_t)K * kSymBlock * 32;
-    z.cost_bytes = align_up(4 * (size_t)z.T, 256) + align_up(8 * (size_t)(z.T + 1), 256) +
+    z.fx_bytes = 8 * 8 * (size_t)(z.nb * kSymBlock);  // 4 components x 2 words per slot
+    z.cost_bytes = 256 + align_up(4 * (size_t)z.T, 256) + align_up(8 * (size_t)(z.T + 1), 256) +
                    8 * (size_t)(z.ctas + 1);
     return z;
 }
 
+SymLayout sym_layout(char *ws, const WsLayout &L) {
+    const SymSizes z = sym_sizes(L.Np);
+    SymLayout y;
+    char *c = ws + L.sym_cost;
+    y.fx_exp = reinterpret_cast<int *>(c);
+    y.cost = reinterpret_cast<uint32_t *>(c + 256);
+    y.prefix = reinterpret_cast<unsigned long long *>(c + 256 + align_up(4 * (size_t)z.T, 256));
+    y.lo = reinterpret_cast<int64_t *>(c + 256 + align_up(4 * (size_t)z.T, 256) +
+                                       align_up(8 * (size_t)(z.T + 1), 256));
+    y.acc_fx = reinterpret_cast<unsigned long long *>(ws + L.sym_fx);
+    return y;
+}
+
 int launch_force_sym(const ForceJob &j, bool adaptive) {
     if (j.eps <= 0.0) return fail(NB_ERR_UNSUPPORTED, "symmetric pairs need eps > 0");
-    if (j.L.sym_rec_bytes == 0)
+    if (j.L.sym_fx_bytes == 0)
         return fail(NB_ERR_WORKSPACE, "workspace has no symmetric-pair buffers");
     const SymSizes z = sym_sizes(j.L.Np);
+    const SymLayout y = sym_layout(j.ws, j.L);
     SymParams p;
     char *sb = j.ws + j.L.sortbuf;
     p.soa = reinterpret_cast<const float *>(j.ws + j.L.packA);
-    p.Np = j.L.Np;
+    p.Np = z.nb * kSymBlock;
     p.nb = z.nb;
     p.T = z.T;
     p.U = z.U;
     p.ctas = z.ctas;
-    p.K = z.K;
     const float ef = (float)j.eps;
     p.eps2 = ef * ef;
     p.gamma = j.gamma;
     p.jbox = adaptive ? sort_tile_boxes(sb, j.L) : nullptr;
     p.wbox = adaptive ? sort_block_boxes(sb, j.L) : nullptr;
-    p.P = reinterpret_cast<float *>(j.ws + j.L.sym_p);
-    p.rec = reinterpret_cast<double *>(j.ws + j.L.sym_rec);
-    p.lo = reinterpret_cast<const int64_t *>(j.ws + j.L.sym_cost + align_up(4 * (size_t)z.T, 256) +
-                                             align_up(8 * (size_t)(z.T + 1), 256));
+    p.acc_fx = y.acc_fx;
+    p.fx_exp = y.fx_exp;
+    p.lo = y.lo;
     const int *perm = adaptive ? sort_perm(sb, j.L) : nullptr;
-    uint32_t *status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
-    p.status = status;
+    p.status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     const int mode = adaptive ? 2 : (j.split ? 1 : 0);
     if (j.precision == NB_PREC_FP64) {
         SymParams64 p64;
@@ -801,13 +761,12 @@ int launch_force_sym(const ForceJob &j, bool adaptive) {
         p64.mass64 = j.mass;
         p64.N = j.N;
         p64.eps2_64 = j.eps * j.eps;
-        p64.P64 = reinterpret_cast<double *>(j.ws + j.L.sym_p);
-        return launch_sym64(p64, j, status);
+        return launch_sym64(p64, j, y);
     }
     switch (j.precision) {
-        case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, mode, perm, status);
-        case NB_PREC_KAHAN: return launch_sym_pol<NB_PREC_KAHAN>(p, j, mode, perm, status);
-        case NB_PREC_F64ACC: return launch_sym_pol<NB_PREC_F64ACC>(p, j, mode, perm, status);
+        case NB_PREC_FP32: return launch_sym_pol<NB_PREC_FP32>(p, j, y, mode, perm);
+        case NB_PREC_KAHAN: return launch_sym_pol<NB_PREC_KAHAN>(p, j, y, mode, perm);
+        case NB_PREC_F64ACC: return launch_sym_pol<NB_PREC_F64ACC>(p, j, y, mode, perm);
     }
     return fail(NB_ERR_INVALID, "unknown precision %d", j.precision);
 }

@@ -149,24 +149,29 @@ def test_pairs_option_and_symmetric_workspace(B):
     assert o.pairs == B.NB_PAIRS_DEFAULT
     n = 1 << 20
     nb = n // 2048
-    partials = nb * (nb - 1) // 2 * 2048 * 16  # FP32 (a, phi) per j-block slot and block pair
     default = B.nb_workspace_bytes(n, 1, o)
     direct = B.nb_workspace_bytes(n, 1, _opts(B, pairs=B.NB_PAIRS_DIRECT))
-    assert default - direct >= partials
+    # the symmetric path adds O(N) scratch: 64 B of fixed-point totals per
+    # slot plus 12 B of cost estimates per block pair
+    extra = default - direct
+    assert 64 * n <= extra <= 64 * n + 12 * nb * (nb + 1) // 2 + 64 * 1024
+    assert default <= 512 << 20
+    n4 = 1 << 22
+    extra4 = (B.nb_workspace_bytes(n4, 1, o)
+              - B.nb_workspace_bytes(n4, 1, _opts(B, pairs=B.NB_PAIRS_DIRECT)))
+    assert extra4 <= 4.5 * extra
     # below the default range only an explicit request provisions the path
     small_default = B.nb_workspace_bytes(1000, 1, o)
     small_sym = B.nb_workspace_bytes(1000, 1, _opts(B, pairs=B.NB_PAIRS_SYMMETRIC))
     assert small_sym > small_default
-    # FP64 pairs keep FP64 partials (twice the bytes) and leave the default
-    # range above 2^20; batches take the batched path instead
+    # FP64 pairs use the same fixed-point totals; above 2^24 the default is
+    # the direct kernel
     fp64 = _opts(B, precision=B.NB_PREC_FP64)
     fp64_direct = _opts(B, precision=B.NB_PREC_FP64, pairs=B.NB_PAIRS_DIRECT)
-    assert (B.nb_workspace_bytes(n, 1, fp64) - B.nb_workspace_bytes(n, 1, fp64_direct)
-            >= 2 * partials)
-    above = n + 2048
-    assert (B.nb_workspace_bytes(above, 1, fp64)
-            == B.nb_workspace_bytes(above, 1, fp64_direct))
-    assert B.nb_workspace_bytes(n, 4, o) < default
+    assert B.nb_workspace_bytes(n, 1, fp64) - B.nb_workspace_bytes(n, 1, fp64_direct) == extra
+    above = (1 << 24) + 2048
+    assert B.nb_workspace_bytes(above, 1, o) == \
+        B.nb_workspace_bytes(above, 1, _opts(B, pairs=B.NB_PAIRS_DIRECT))
 
 
 def test_unknown_pairs_mode_is_rejected(B):

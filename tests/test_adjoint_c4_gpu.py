@@ -10,12 +10,21 @@ scalars:
 * FP64-pair gradient vs the oracle's unmerged step adjoint: <= 1e-9;
 * FP32-pair, FP64-accumulate gradient vs the oracle: median <= 1e-4,
   max <= 1e-3;
-* central differences (h = 1e-6, 1e-6 m_k for masses) of the FP64-pair GPU
-  forward map vs the oracle's gradient: <= 1e-6.
+* finite differences of the FP64-pair GPU forward map vs the oracle's
+  gradient: <= 1e-6 relative plus the loss's rounding noise over the step
+  (central differences with h = 1e-6 for positions and velocities; for
+  masses, whose gradients are smallest, a four-point stencil with
+  h = 1e-2 m_k, truncation error O(h^4)).
 
-The differences are taken of the GPU's FP64-pair map, not the oracle's: 128
-oracle runs of 200 steps at this size take about 25 minutes on 16 host
-cores, while the FP64 GPU map agrees with the oracle's to ~1e-12.
+The loss's FP64 rounding noise: the final positions carry ~|x| u sqrt(200)
+~ 2e-15 of accumulated rounding, so L = (1/N) sum |x_i - x*_i|^2 with
+|x_i - x*_i| ~ 1e-3 moves by ~(2/N) 1e-3 2e-15 sqrt(N) ~ 3e-20 from run to
+run of nearly equal inputs; the gate allows ETA = 1e-18 of it per loss
+value.  (Step sizes of 1e-6 m_k for masses, first tried, leave that noise
+at up to 10 % of their gradients.)  The differences are taken of the GPU's
+FP64-pair map, not the oracle's: about 150 oracle runs of 200 steps at this
+size take about half an hour on 16 host cores, while the FP64 GPU map
+agrees with the oracle's to ~1e-12.
 """
 import numpy as np
 import pytest
@@ -74,7 +83,10 @@ def test_f64acc_gradient_matches_oracle(workload, mode):
     assert np.median(rel) <= 1e-4 and rel.max() <= 1e-3, (mode, np.median(rel), rel.max())
 
 
-def test_central_differences_match_oracle_gradient(workload):
+ETA = 1e-18  # bound on the FP64 rounding noise of one loss value
+
+
+def test_finite_differences_match_oracle_gradient(workload):
     s, target, _, ref, coords = workload
     sysm = api.System(s.pos, s.vel, s.mass, EPS, precision="fp64", pairs="symmetric")
     tgt = torch.tensor(target, device="cuda")
@@ -87,22 +99,29 @@ def test_central_differences_match_oracle_gradient(workload):
         sysm.step(H, STEPS)
         return float(((sysm.pos - tgt) ** 2).sum() / N)
 
-    fd = np.empty(len(coords))
-    for k, c in enumerate(coords):
-        vals = []
-        for sign in (1, -1):
-            p, v, m = s.pos.copy(), s.vel.copy(), s.mass.copy()
-            if c < 3 * N:
-                step = 1e-6
-                p.reshape(-1)[c] += sign * step
-            elif c < 6 * N:
-                step = 1e-6
-                v.reshape(-1)[c - 3 * N] += sign * step
-            else:
-                step = 1e-6 * s.mass[c - 6 * N]
-                m[c - 6 * N] += sign * step
-            vals.append(loss(p, v, m))
-        fd[k] = (vals[0] - vals[1]) / (2 * step)
+    def shifted(c, d):
+        p, v, m = s.pos.copy(), s.vel.copy(), s.mass.copy()
+        if c < 3 * N:
+            p.reshape(-1)[c] += d
+        elif c < 6 * N:
+            v.reshape(-1)[c - 3 * N] += d
+        else:
+            m[c - 6 * N] += d
+        return loss(p, v, m)
+
+    bad = []
+    for c in coords:
+        g = ref[c]
+        if c < 6 * N:
+            h = 1e-6
+            fd = (shifted(c, h) - shifted(c, -h)) / (2 * h)
+            noise = ETA / h
+        else:
+            h = 1e-2 * s.mass[c - 6 * N]
+            fd = (8 * (shifted(c, h) - shifted(c, -h)) - (shifted(c, 2 * h) - shifted(c, -2 * h))) \
+                / (12 * h)
+            noise = 1.5 * ETA / h
+        if abs(fd - g) > 1e-6 * abs(g) + noise:
+            bad.append((int(c), fd, g, noise))
     assert binding.NB_OK == sysm.poll()
-    rel = _rel(fd, ref[coords], ref)
-    assert rel.max() <= 1e-6, (rel.max(), coords[np.argmax(rel)])
+    assert not bad, bad

@@ -3,11 +3,14 @@
 Each unordered pair is evaluated once and applied to both particles (Eq. 1
 changes sign under i <-> j apart from the masses).  Covered: 1, 2, 3 and 17
 row blocks of 2048 slots with ragged last blocks, the three displacement
-modes and three FP32-pair policies, the fold of j-side partials and row
-records, the fused closing half-kick of a step loop (and the Hilbert order
-kept across steps), G scaling, a missing potential output, run-to-run
-bitwise determinism, agreement with the direct path, and the host-side
-refusals (eps = 0, a workspace sized for the direct path).
+modes and three FP32-pair policies, the fixed-point combination of j-side
+partials and row totals across CTAs, the fused closing half-kick of a step
+loop (and the Hilbert order kept across steps), G scaling, a missing
+potential output, run-to-run bitwise determinism, agreement with the direct
+path, a 2^22 + 777-particle evaluation on sampled rows, a small softening
+length (the fixed-point grid against the FP64 gate), the host-side refusals
+(eps = 0, a workspace sized for the direct path) and the kernel timer past
+its 64 event pairs.
 """
 import numpy as np
 import pytest
@@ -127,16 +130,18 @@ def test_refusals():
     assert rel_vec_err(a, ra).max() <= 1e-5
 
 
-def test_top_of_default_range_sampled_rows():
-    # 2^21 - 12345 particles: 1024 row blocks with a ragged last one, the
-    # largest default symmetric evaluation (17 GB of j-side partials)
-    n = (1 << 21) - 12345
-    s = ics.plummer(n, seed=21)
+@pytest.mark.slow
+def test_four_million_particles_sampled_rows():
+    # 2^22 + 777 particles: 2049 row blocks with a ragged last one (scratch
+    # O(N): 64 B per particle of fixed-point totals)
+    n = (1 << 22) + 777
+    s = ics.plummer(n, seed=22)
     r = np.linalg.norm(s.pos, axis=1)
     order = np.argsort(r)
     rows = np.unique(np.concatenate([np.random.default_rng(8).choice(n, 400, replace=False),
                                      order[:32], order[-32:], np.arange(n - 40, n)]))
     o = binding.make_opts("kahan")
+    assert binding.nb_workspace_bytes(n, 1, o) <= 2 << 30
     acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     pot = torch.empty(n, dtype=torch.float64, device="cuda")
     ws = binding.workspace(n, 1, o)
@@ -146,6 +151,17 @@ def test_top_of_default_range_sampled_rows():
     assert rel_vec_err(host(acc)[rows], ra).max() <= 1e-5
     assert rel_err(host(pot)[rows], rp).max() <= 1e-5
     del ws
+
+
+def test_small_softening_fixed_point_grid():
+    # eps = 1e-6 raises the a-priori bound that fixes the fixed-point grid
+    # (N max|m| 0.385 / eps^2); FP64 pairs still meet the FP64 gate
+    s = _system(40000, 9)
+    ra, rp = oracle.forces(s.pos, s.mass, 1e-6)
+    a, p = _forces(s, 1e-6, "fp64")
+    assert rel_vec_err(a, ra).max() <= 1e-12 and rel_err(p, rp).max() <= 1e-12
+    a1, p1 = _forces(s, 1e-6, "fp64")
+    assert np.array_equal(a, a1) and np.array_equal(p, p1)
 
 
 @pytest.mark.parametrize("n", [1, 2, 100, 2049, 5000, 34000])
@@ -196,3 +212,10 @@ def test_kernel_timing_hook_times_each_pair_launch():
     api.forces(pos, mass, 1e-3, precision="kahan")
     torch.cuda.synchronize()
     assert binding.nb_kernel_time()[1] == 3
+    # more launches than the ring's 64 event pairs: the oldest are folded in
+    binding.nb_kernel_timing(True)
+    for _ in range(70):
+        api.forces(pos, mass, 1e-3, precision="kahan")
+    ms70, n70 = binding.nb_kernel_time()
+    binding.nb_kernel_timing(False)
+    assert n70 == 70 and ms70 > 10 * ms / 3

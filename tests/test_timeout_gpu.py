@@ -10,8 +10,8 @@ The tests check that nb_poll_status reports the timeout, and that after the
 caller re-zeroes the workspace (the arrival counters of an interrupted call
 are left behind, as nbody.h states) the next call with the default bound
 matches the oracle.  Whether a particular wait finds its stage complete
-depends on timing, so a call is repeated (with the L2 flushed first) until
-one reports the timeout; a call that did not is checked like any other.
+depends on timing (a stage issued long before its wait has landed), so a
+call is repeated (with the L2 flushed first) until one reports the timeout.
 """
 import numpy as np
 import pytest
@@ -23,7 +23,7 @@ from tests.gpu_util import TOL, dev, host, rel_err, rel_vec_err
 
 pytestmark = pytest.mark.gpu
 
-ATTEMPTS = 5
+ATTEMPTS = 20
 
 
 @pytest.fixture(scope="module", autouse=True)
