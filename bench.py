@@ -18,9 +18,11 @@ initial positions ("accuracy": gated at 1e-5 in the tests).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank advances its own replica (no data exchange:
-the single-system workload does not shard without an all-gather, which this
-library does not implement), value = all ranks' interactions / max time.
+Under torchrun (N > 1) every rank advances its own replica of the 2^20 step
+(weak scaling, no data exchange), value = all ranks' interactions / max
+time; the "sharded" object beside it times the same system split over the
+ranks by rows (strong scaling: nb_forces_range per rank, one NCCL
+all-gather of the positions per step), also at N = 1 as its baseline.
 """
 from __future__ import annotations
 
@@ -415,6 +417,39 @@ def adjoint_ratio(torch):
                                          precision="f64acc")
 
 
+def sharded_rate(torch, args, ws, dev):
+    """The 2^20 workload with its rows split over the ranks (strong scaling:
+    the same system on every N): contiguous particle ranges, one position
+    all-gather per step (NCCL), nb_forces_range for each rank's rows (the
+    direct kernel) and the kick / drift of the rows; max over ranks of the
+    CUDA-event time of the timed steps."""
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import ShardedSystem
+    s = ics.plummer(N_MAIN, seed=0)
+    g = ShardedSystem(s.pos, s.vel, s.mass, EPS_MAIN, precision="kahan", device=dev)
+    for _ in range(args.warmup):
+        g.step(DT_MAIN, 1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.step(DT_MAIN, args.steps)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        ms = max_over_ranks(ms, dev)
+    return {"workload": "Plummer N=2^20, eps=1e-3, KDK steps dt=1e-4, rows split over "
+                        f"{ws} rank(s) in contiguous ranges (Kahan, direct kernel per rank, "
+                        "one FP64 position all-gather per step)",
+            "scaling": "strong", "n_gpus": ws, "steps": args.steps,
+            "ms_per_step": ms / args.steps,
+            "value": args.steps * float(N_MAIN) ** 2 / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "rows_per_rank": g.c, "status": g.ops.poll()}
+
+
 def run_ours(args):
     import torch
 
@@ -512,7 +547,12 @@ def run_ours(args):
     d2h = sum(v.numel() * 8 for v in outs.values()) + 24
     del e2e_sys
 
-    adj = batched = variants = paper = None
+    adj = batched = variants = paper = sharded = None
+    if not args.skip_extra:
+        try:
+            sharded = sharded_rate(torch, args, ws, dev)
+        except Exception as e:
+            sharded = {"error": f"{type(e).__name__}: {e}"}
     if not args.skip_adjoint:
         try:
             adj = adjoint_ratio(torch)
@@ -596,6 +636,7 @@ def run_ours(args):
                      "lognormal_65536_per_precision": variants},
         "adjoint": adj,
         "batched": batched,
+        "sharded": sharded,
         "paper_workload": paper,
     }
     if ws == 1 and not args.skip_cpu:

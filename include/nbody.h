@@ -146,6 +146,18 @@ typedef struct nb_opts {
                                coordinate magnitude; 0 = default (1/64;
                                1/256 on the batched symmetric path)       */
     int32_t pairs;          /* nb_pairs                                       */
+    int32_t test_unissued_stage; /* test hook, 0 = off.  k > 0: the direct-pair
+                               kernels that stage j-tiles through a ring of
+                               bulk copies (nb_forces / nb_forces_range /
+                               nb_forces_noalloc on the direct path,
+                               nb_forces_vjp and the step adjoints,
+                               nb_forces_jerk / nb_hermite4) never issue the
+                               copies of their k-th stage in each CTA, so the
+                               bounded wait on it runs out after
+                               timeout_cycles and NB_ERR_TIMEOUT is latched:
+                               how a test exercises the device-side timeout
+                               path without a fault.  Results are then
+                               undefined and the workspace needs re-zeroing. */
 } nb_opts;
 
 /* Fills *opts with precision F64ACC, G = 1, default stream, no graph,
@@ -209,6 +221,38 @@ size_t nb_workspace_bytes(int64_t N_total, int32_t B, const nb_opts *opts);
  */
 int nb_forces(const double *pos, const double *mass, int64_t N, double eps, double *acc,
               double *pot, void *ws, size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * Accelerations and potentials of the particles i0 .. i1-1 of a system of N
+ * (Eq. 1 for those rows only, each against all N).  This is one rank's
+ * share when the particles of one system are split over several GPUs in
+ * contiguous ranges -- the data decomposition of Sec. 3.2 (approach 1):
+ * every rank holds all N positions (gathered each step) and evaluates its
+ * own rows; no other exchange is needed for the forces.
+ *   pos [N][3], mass [N]          all particles (inputs)
+ *   0 <= i0 < i1 <= N             the rows
+ *   acc [i1-i0][3]                output rows, overwritten
+ *   pot [i1-i0] or NULL           output rows, overwritten when non-NULL
+ * Every ordered pair of the rows is evaluated (the direct kernel, whatever
+ * opts->pairs says); positions ADAPTIVE is taken as SPLIT.  The workspace
+ * is sized for the whole system: nb_workspace_bytes(N, 1, opts).
+ * Returns NB_ERR_INVALID for a bad range and as nb_forces otherwise.
+ */
+int nb_forces_range(const double *pos, const double *mass, int64_t N, int64_t i0, int64_t i1,
+                    double eps, double *acc, double *pot, void *ws, size_t ws_bytes,
+                    const nb_opts *opts);
+
+/*
+ * The kick and drift of kick-drift-kick leapfrog for n particles, in FP64:
+ *   vel += kick * acc;   pos += drift * vel   (the updated vel)
+ * pos, vel, acc device [n][3].  A KDK step of size h whose force evaluation
+ * the caller drives itself (nb_forces_range on several GPUs) is
+ * nb_kick_drift(h/2, h), the evaluation at the new positions, then
+ * nb_kick_drift(h/2, 0).  NB_ERR_INVALID for n < 1, NULL or misaligned
+ * arrays, non-finite kick or drift.
+ */
+int nb_kick_drift(double *pos, double *vel, const double *acc, int64_t n, double kick,
+                  double drift, const nb_opts *opts);
 
 /*
  * nb_forces for callers that cannot allocate device memory and therefore

@@ -45,7 +45,7 @@ EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
             "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4",
-            "nb_kernel_timing", "nb_kernel_time")
+            "nb_kernel_timing", "nb_kernel_time", "nb_forces_range", "nb_kick_drift")
 
 
 class NbError(RuntimeError):
@@ -70,7 +70,7 @@ class nb_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32),
                 ("tune", ctypes.POINTER(nb_tune)), ("timeout_cycles", ctypes.c_int64),
                 ("positions", ctypes.c_int32), ("near_gamma", ctypes.c_float),
-                ("pairs", ctypes.c_int32)]
+                ("pairs", ctypes.c_int32), ("test_unissued_stage", ctypes.c_int32)]
 
 
 class nb_state(ctypes.Structure):
@@ -112,6 +112,9 @@ _SIGS = {
     "nb_forces_jerk": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _sz, _OPTS]),
     "nb_hermite4": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _vp, _vp, _i32, _d, _i64, _vp, _sz,
                                    _OPTS]),
+    "nb_forces_range": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _d, _vp, _vp, _vp, _sz,
+                                       _OPTS]),
+    "nb_kick_drift": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _d, _OPTS]),
 }
 
 
@@ -155,7 +158,7 @@ def _dptr(t, name, dtype=None, optional=False):
 
 def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool = False,
               tune=None, timeout_cycles: int = 0, positions="default",
-              near_gamma: float = 0.0, pairs="default") -> nb_opts:
+              near_gamma: float = 0.0, pairs="default", test_unissued_stage: int = 0) -> nb_opts:
     """nb_opts for a call; stream None = torch's current stream on the current device."""
     o = nb_opts()
     lib().nb_opts_default(ctypes.byref(o))
@@ -175,6 +178,7 @@ def make_opts(precision="f64acc", G: float = 1.0, stream=None, use_graph: bool =
     o.positions = POSITIONS[positions] if isinstance(positions, str) else int(positions)
     o.near_gamma = float(near_gamma)
     o.pairs = PAIRS[pairs] if isinstance(pairs, str) else int(pairs)
+    o.test_unissued_stage = int(test_unissued_stage)
     return o
 
 
@@ -227,6 +231,26 @@ def nb_forces(pos, mass, eps: float, acc, pot, ws, opts: nb_opts):
     _check(lib().nb_forces(_dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n, float(eps),
                            _dptr(acc, "acc", f64), _dptr(pot, "pot", f64, True),
                            _dptr(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_forces_range(pos, mass, i0: int, i1: int, eps: float, acc, pot, ws, opts: nb_opts):
+    """Rows i0..i1-1 of the forces of all N particles (acc/pot hold i1-i0 rows)."""
+    import torch
+    f64 = torch.float64
+    n = mass.shape[0]
+    _check(lib().nb_forces_range(_dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n, int(i0),
+                                 int(i1), float(eps), _dptr(acc, "acc", f64),
+                                 _dptr(pot, "pot", f64, True), _dptr(ws, "ws"),
+                                 ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_kick_drift(pos, vel, acc, kick: float, drift: float, opts: nb_opts):
+    """vel += kick acc; pos += drift vel (n = rows of vel)."""
+    import torch
+    f64 = torch.float64
+    _check(lib().nb_kick_drift(_dptr(pos, "pos", f64), _dptr(vel, "vel", f64),
+                               _dptr(acc, "acc", f64), vel.shape[0], float(kick), float(drift),
+                               ctypes.byref(opts)))
 
 
 def nb_forces_noalloc(pos, mass, eps: float, acc, pot, opts: nb_opts):

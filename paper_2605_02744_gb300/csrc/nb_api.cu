@@ -294,6 +294,7 @@ static int check_common(const nb_opts *o, int64_t N, double eps) {
     if (o->precision < NB_PREC_FP32 || o->precision > NB_PREC_FP64)
         return fail(NB_ERR_INVALID, "unknown precision %d", o->precision);
     if (o->timeout_cycles < 0) return fail(NB_ERR_INVALID, "timeout_cycles must be >= 0");
+    if (o->test_unissued_stage < 0) return fail(NB_ERR_INVALID, "test_unissued_stage must be >= 0");
     if (o->positions < NB_POS_DEFAULT || o->positions > NB_POS_ADAPTIVE)
         return fail(NB_ERR_INVALID, "unknown positions mode %d", o->positions);
     if (o->pairs < NB_PAIRS_DEFAULT || o->pairs > NB_PAIRS_SYMMETRIC)
@@ -305,6 +306,10 @@ static int check_common(const nb_opts *o, int64_t N, double eps) {
 
 static long long timeout_of(const nb_opts *o) {
     return o->timeout_cycles > 0 ? (long long)o->timeout_cycles : kDefaultTimeoutCycles;
+}
+
+static int64_t unissued_of(const nb_opts *o) {
+    return o->test_unissued_stage > 0 ? (int64_t)o->test_unissued_stage - 1 : -1;
 }
 
 #define NB_TRY(expr)              \
@@ -328,6 +333,8 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     j->pos = pos;
     j->mass = mass;
     j->N = N;
+    j->i0 = 0;
+    j->ni = N;
     j->eps = eps;
     j->G = o->G;
     j->acc = acc;
@@ -344,6 +351,7 @@ static int make_force_job(ForceJob *j, const double *pos, const double *mass, in
     // an explicit NB_PAIRS_SYMMETRIC with eps = 0 is refused by the launcher
     j->sym = sym_wanted(o, N, 1) && (eps > 0.0 || o->pairs == NB_PAIRS_SYMMETRIC);
     j->timeout = timeout_of(o);
+    j->unissued = unissued_of(o);
     j->stream = (cudaStream_t)o->stream;
     j->ws = (char *)ws;
     return NB_OK;
@@ -459,6 +467,37 @@ int nb_forces(const double *pos, const double *mass, int64_t N, double eps, doub
     return launch_force(j);
 }
 
+int nb_forces_range(const double *pos, const double *mass, int64_t N, int64_t i0, int64_t i1,
+                    double eps, double *acc, double *pot, void *ws, size_t ws_bytes,
+                    const nb_opts *opts) {
+    clear_error();
+    if (i0 < 0 || i1 <= i0 || i1 > N)
+        return fail(NB_ERR_INVALID, "need 0 <= i0 < i1 <= N (got i0 = %lld, i1 = %lld, N = %lld)",
+                    (long long)i0, (long long)i1, (long long)N);
+    ForceJob j;
+    NB_TRY(make_force_job(&j, pos, mass, N, eps, acc, pot, ws, ws_bytes, opts));
+    j.i0 = i0;
+    j.ni = i1 - i0;
+    // rows of the whole system in particle order: the direct kernel, no
+    // Hilbert sort (ADAPTIVE is taken as SPLIT)
+    j.sym = false;
+    j.adaptive = false;
+    return launch_force(j);
+}
+
+int nb_kick_drift(double *pos, double *vel, const double *acc, int64_t n, double kick,
+                  double drift, const nb_opts *o) {
+    clear_error();
+    if (!o) return fail(NB_ERR_INVALID, "opts is NULL");
+    if (n < 1) return fail(NB_ERR_INVALID, "n must be >= 1");
+    if (!isfinite(kick) || !isfinite(drift))
+        return fail(NB_ERR_INVALID, "kick and drift must be finite");
+    NB_TRY(check_ptr(pos, "pos"));
+    NB_TRY(check_ptr(vel, "vel"));
+    NB_TRY(check_ptr(acc, "acc"));
+    return launch_kick_drift(pos, vel, acc, n, kick, drift, (cudaStream_t)o->stream);
+}
+
 int nb_forces_batched(const double *pos, const double *mass, const int64_t *offsets, int32_t B,
                       int64_t N, const double *eps, double *acc, double *pot, void *ws,
                       size_t ws_bytes, const nb_opts *o) {
@@ -500,6 +539,7 @@ int nb_forces_batched(const double *pos, const double *mass, const int64_t *offs
     j.gamma = o->near_gamma;
     j.sym = bsym_wanted(o, N, B);
     j.timeout = timeout_of(o);
+    j.unissued = unissued_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)ws;
     return launch_batched(j);
@@ -530,6 +570,7 @@ static int step_batched_direct(nb_state *s, double dt, int64_t nsteps, const nb_
     j.gamma = o->near_gamma;
     j.sym = bsym_wanted(o, s->N, s->B);
     j.timeout = timeout_of(o);
+    j.unissued = unissued_of(o);
     j.stream = (cudaStream_t)o->stream;
     j.ws = (char *)s->ws;
     return launch_batched(j);
@@ -618,6 +659,7 @@ int nb_step(nb_state *s, double dt, int64_t nsteps, const nb_opts *o) {
         key.o.stream = o->stream;
         key.o.use_graph = o->use_graph;
         key.o.timeout_cycles = o->timeout_cycles;
+        key.o.test_unissued_stage = o->test_unissued_stage;
         key.o.positions = o->positions;
         key.o.near_gamma = o->near_gamma;
         key.o.pairs = o->pairs;
@@ -707,6 +749,7 @@ static int make_vjp_job(VjpJob *j, const double *pos, const double *mass, int64_
     // displacements unless the caller asks for the split form
     j->split = o->positions == NB_POS_SPLIT;
     j->timeout = timeout_of(o);
+    j->unissued = unissued_of(o);
     j->stream = (cudaStream_t)o->stream;
     j->ws = (char *)ws;
     return NB_OK;
@@ -794,6 +837,7 @@ static int make_jerk_job(JerkJob *j, double *pos, double *vel, const double *mas
     j->pot = pot;
     j->precision = o->precision;
     j->timeout = timeout_of(o);
+    j->unissued = unissued_of(o);
     j->stream = (cudaStream_t)o->stream;
     j->ws = (char *)ws;
     return NB_OK;

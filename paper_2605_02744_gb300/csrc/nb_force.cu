@@ -66,7 +66,8 @@ int launch_pack(const double *pos, const double *mass, int64_t N, int64_t Np, fl
 struct ForceParams {
     const float *soa;  // [7][Np]: x.hi y.hi z.hi m x.lo y.lo z.lo
     int64_t Np;
-    int64_t N;
+    int64_t i0;   // packed index of the first i-particle (row) of this call
+    int64_t ni;   // rows: i-slot s is packed particle i0 + s, output row s
     int64_t total;  // nblocks * ntiles
     int32_t nblocks;
     int32_t ntiles;
@@ -80,6 +81,7 @@ struct ForceParams {
     uint32_t *counters;
     uint32_t *status;
     long long timeout;
+    int64_t unissued;  // test hook: the ring stage whose copies are never issued (-1: none)
     // adaptive displacement (NF): particles packed in Hilbert order
     const float *tile_box;   // [N/64][8]: lo[3] hi[3] max|x| pad, per 64 j-slots
     const float *block_box;  // [N/(32 IR)][8], per warp's 32 IR i-slots
@@ -104,7 +106,7 @@ __device__ __forceinline__ void force_epilogue(const ForceParams &p, int64_t b,
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
         const int64_t slot = slot_of<NT, IR, NF>(b, k, threadIdx.x);
-        if (slot < p.N) {
+        if (slot < p.ni) {
             const int64_t i = NF ? (int64_t)p.perm[slot] : slot;
             const double phs = acc[k][3].value();
             const double gx = p.G * acc[k][0].value();
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
     __syncthreads();
 
     auto issue = [&](int64_t q) {
+        if (q == p.unissued) return;  // the wait on this stage runs out
         const int s = (int)(q % ST);
         const int64_t jt = (L0 + q) % p.ntiles;
         float *dst = stages + s * NC * TJ;
@@ -234,14 +237,18 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
             }
 #pragma unroll
             for (int k = 0; k < IR; ++k) {
-                const int64_t i = slot_of<NT, IR, NF>(b, k, tid);
-                const float x = p.soa[i], y = p.soa[p.Np + i], z = p.soa[2 * p.Np + i];
+                const int64_t sl = slot_of<NT, IR, NF>(b, k, tid);
+                const bool live = sl < p.ni;  // past the rows: a zero particle
+                const int64_t i = p.i0 + (live ? sl : 0);
+                const float x = live ? p.soa[i] : 0.f, y = live ? p.soa[p.Np + i] : 0.f,
+                            z = live ? p.soa[2 * p.Np + i] : 0.f;
                 nx[k] = f2(-x, -x);
                 ny[k] = f2(-y, -y);
                 nz[k] = f2(-z, -z);
                 if (SPLIT) {
-                    const float xl = p.soa[4 * p.Np + i], yl = p.soa[5 * p.Np + i],
-                                zl = p.soa[6 * p.Np + i];
+                    const float xl = live ? p.soa[4 * p.Np + i] : 0.f,
+                                yl = live ? p.soa[5 * p.Np + i] : 0.f,
+                                zl = live ? p.soa[6 * p.Np + i] : 0.f;
                     nxl[k] = f2(-xl, -xl);
                     nyl[k] = f2(-yl, -yl);
                     nzl[k] = f2(-zl, -zl);
@@ -260,11 +267,13 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
         for (int k = 0; k < IR; ++k) ax[k] = ay[k] = az[k] = ph[k] = f2(0.f, 0.f);
         // a tile that holds some of block b's slots has the self pairs: they
         // take the masked loop (exact j != i); every other tile the plain one
-        const bool diag = jt * TJ < (b + 1) * BI && (jt + 1) * TJ > b * BI;
+        const int64_t r0 = p.i0 + b * BI;  // packed index of the block's first row
+        const bool diag = jt * TJ < r0 + BI && (jt + 1) * TJ > r0;
         if (diag) {
             int kr[IR];
 #pragma unroll
-            for (int k = 0; k < IR; ++k) kr[k] = (int)(slot_of<NT, IR, NF>(b, k, tid) - jt * TJ);
+            for (int k = 0; k < IR; ++k)
+                kr[k] = (int)(p.i0 + slot_of<NT, IR, NF>(b, k, tid) - jt * TJ);
             tile_pairs<IR, TJ, GUARD, SPLIT, true>(sx, 0, TJ, eps2, nx, ny, nz, nxl, nyl, nzl, ax,
                                                    ay, az, ph, kr);
         } else if (NF) {
@@ -301,7 +310,8 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
                 const long long drain = p.timeout > kDefaultTimeoutCycles ? p.timeout
                                                                        : kDefaultTimeoutCycles;
                 for (int64_t r = q; r < nq && r < q + ST; ++r)
-                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
+                    if (r != p.unissued)
+                        mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
             }
             __syncthreads();
             return;
@@ -356,11 +366,12 @@ __global__ void __launch_bounds__(NT) force_sk_kernel(const ForceParams p) {
 template <int NT, bool GUARD>
 __global__ void __launch_bounds__(NT)
     force_fp64_kernel(const double *__restrict__ pos, const double *__restrict__ mass, int64_t N,
-                      double eps2, double G, double *acc, double *pot, double *vel, double kick,
-                      uint32_t *status) {
+                      int64_t i0, int64_t ni, double eps2, double G, double *acc, double *pot,
+                      double *vel, double kick, uint32_t *status) {
     __shared__ double sx[NT], sy[NT], sz[NT], sm[NT];
-    const int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
-    const bool live = i < N;
+    const int64_t row = blockIdx.x * (int64_t)NT + threadIdx.x;  // output row
+    const int64_t i = i0 + row;                                   // particle
+    const bool live = row < ni;
     const double xi = live ? pos[3 * i] : 0.0;
     const double yi = live ? pos[3 * i + 1] : 0.0;
     const double zi = live ? pos[3 * i + 2] : 0.0;
@@ -392,14 +403,14 @@ __global__ void __launch_bounds__(NT)
     }
     if (live) {
         const double gx = G * ax, gy = G * ay, gz = G * az, gp = -G * ph;
-        acc[3 * i] = gx;
-        acc[3 * i + 1] = gy;
-        acc[3 * i + 2] = gz;
-        if (pot) pot[i] = gp;
+        acc[3 * row] = gx;
+        acc[3 * row + 1] = gy;
+        acc[3 * row + 2] = gz;
+        if (pot) pot[row] = gp;
         if (vel) {
-            vel[3 * i] += kick * gx;
-            vel[3 * i + 1] += kick * gy;
-            vel[3 * i + 2] += kick * gz;
+            vel[3 * row] += kick * gx;
+            vel[3 * row + 1] += kick * gy;
+            vel[3 * row + 2] += kick * gz;
         }
         if (!(isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(gp)))
             dev::set_status(status, kStatusNonFinite);
@@ -489,14 +500,15 @@ int launch_force(const ForceJob &j) {
             return launch_force_sym(j, false);
         }
         constexpr int NT = 128;
-        const int64_t grid = cdiv(j.N, NT);
+        const int64_t grid = cdiv(j.ni, NT);
         count_launch();
         if (guard)
             force_fp64_kernel<NT, true><<<(unsigned)grid, NT, 0, j.stream>>>(
-                j.pos, j.mass, j.N, 0.0, j.G, j.acc, j.pot, j.vel, j.kick, status);
+                j.pos, j.mass, j.N, j.i0, j.ni, 0.0, j.G, j.acc, j.pot, j.vel, j.kick, status);
         else
             force_fp64_kernel<NT, false><<<(unsigned)grid, NT, 0, j.stream>>>(
-                j.pos, j.mass, j.N, j.eps * j.eps, j.G, j.acc, j.pot, j.vel, j.kick, status);
+                j.pos, j.mass, j.N, j.i0, j.ni, j.eps * j.eps, j.G, j.acc, j.pot, j.vel, j.kick,
+                status);
         NB_CUDA(cudaGetLastError());
         return NB_OK;
     }
@@ -508,8 +520,8 @@ int launch_force(const ForceJob &j) {
     if (adaptive) {
         // boxes per 64 j-slots and per warp of i-slots (direct kernel), or per
         // 32-slot j-set and 128-slot warp i-set (symmetric kernel)
-        const int tile_unit = j.sym ? 32 : 64;
-        const int block_unit = j.sym ? 128 : 32 * sh0.ipt;
+        const int tile_unit = j.sym ? (sym_jpair() ? 64 : 32) : 64;
+        const int block_unit = j.sym ? (sym_jpair() == 1 ? 256 : 128) : 32 * sh0.ipt;
         int rc = launch_sorted_pack(j.pos, j.mass, j.N, j.L.Np, soa, sort_perm(sb, j.L),
                                     sort_keys(sb), sort_box6(sb, j.L), sort_tile_boxes(sb, j.L),
                                     tile_unit, sort_block_boxes(sb, j.L), block_unit,
@@ -524,8 +536,9 @@ int launch_force(const ForceJob &j) {
     ForceParams p;
     p.soa = soa;
     p.Np = j.L.Np;
-    p.N = j.N;
-    p.nblocks = (int32_t)cdiv(j.N, sh.block_i());
+    p.i0 = j.i0;
+    p.ni = j.ni;
+    p.nblocks = (int32_t)cdiv(j.ni, sh.block_i());
     p.ntiles = (int32_t)cdiv(j.N, sh.tile_j);
     p.total = (int64_t)p.nblocks * p.ntiles;
     const float eps_f = (float)j.eps;
@@ -539,6 +552,7 @@ int launch_force(const ForceJob &j) {
     p.counters = reinterpret_cast<uint32_t *>(j.ws + j.L.counters);
     p.status = status;
     p.timeout = j.timeout;
+    p.unissued = j.unissued;
     p.tile_box = adaptive ? sort_tile_boxes(sb, j.L) : nullptr;   // per 64 j-slots
     p.block_box = adaptive ? sort_block_boxes(sb, j.L) : nullptr; // per warp (32 IR i-slots)
     p.perm = adaptive ? sort_perm(sb, j.L) : nullptr;

@@ -104,6 +104,8 @@ struct ForceJob {
     const double *pos;
     const double *mass;
     int64_t N;
+    int64_t i0, ni;     // rows: particles i0 .. i0 + ni - 1 (all N: 0, N); acc/pot
+                        // hold ni rows.  A strict sub-range takes the direct kernel.
     double eps;
     double G;
     double *acc;
@@ -119,6 +121,7 @@ struct ForceJob {
     bool packed_ready;  // packA already holds float positions of `pos`
     bool sym;           // symmetric-pair evaluation (nb_pairs resolved)
     long long timeout;
+    int64_t unissued;  // test hook (nb_opts.test_unissued_stage - 1; -1: off)
     cudaStream_t stream;
     char *ws;
     WsLayout L;
@@ -211,6 +214,10 @@ struct SymLayout {
     unsigned long long *acc_fx;    // [4][2][Np]
 };
 SymLayout sym_layout(char *ws, const WsLayout &L);
+// Which symmetric kernel: 0 = 32-slot j-sets / 128-slot warp i-sets,
+// 1 = j-pair kernel with 8 warps of 256 i-slots, 2 = j-pair with 16 warps
+// of 128 (both with 64-slot j-sets).
+int sym_jpair();
 // Whether the symmetric-pair path is provisioned / taken for N particles in
 // B clusters under opts (nb_pairs; FP32-pair policies, single systems).
 bool sym_wanted(const nb_opts *opts, int64_t N, int32_t B);
@@ -243,6 +250,7 @@ struct VjpJob {
     int precision;
     bool split;  // hi/lo displacement (the VJP's default is single floats)
     long long timeout;
+    int64_t unissued;  // test hook (nb_opts.test_unissued_stage - 1; -1: off)
     cudaStream_t stream;
     char *ws;
     WsLayout L;
@@ -252,6 +260,9 @@ int launch_vjp(const VjpJob &job);
 
 int launch_kick_drift_pack(double *pos, double *vel, const double *acc, const double *mass,
                            int64_t N, int64_t Np, double dt, float *soa, cudaStream_t st);
+// v += kick a; x += drift v for n particles (FP64).
+int launch_kick_drift(double *pos, double *vel, const double *acc, int64_t n, double kick,
+                      double drift, cudaStream_t st);
 int launch_energy(const double *vel, const double *mass, const double *pot, int64_t N,
                   double *out3, char *ws, const WsLayout &L, cudaStream_t st);
 
@@ -269,6 +280,7 @@ struct JerkJob {
     int64_t nsteps;  // 0 = evaluate a, jerk, phi at the current state
     int precision;
     long long timeout;
+    int64_t unissued;  // test hook (nb_opts.test_unissued_stage - 1; -1: off)
     cudaStream_t stream;
     char *ws;
     WsLayout L;
@@ -297,6 +309,7 @@ struct BatchedJob {
     float gamma;      // near/far threshold (0 = default)
     bool sym;         // symmetric pairs (nb_pairs resolved)
     long long timeout;
+    int64_t unissued;  // test hook (nb_opts.test_unissued_stage - 1; -1: off)
     cudaStream_t stream;
     char *ws;
     WsLayout L;

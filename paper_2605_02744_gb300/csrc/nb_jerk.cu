@@ -43,6 +43,7 @@ struct JerkParams {
     double h;       // corrector step; 0 = store a, jerk, phi only
     uint32_t *status;
     long long timeout;
+    int64_t unissued;  // test hook: the ring stage whose copies are never issued (-1: none)
 };
 
 // Prediction (h > 0) or the current state (h == 0), packed for the kernel:
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
     const int64_t nq = nmine * p.ntiles;
     if (nq <= 0) return;
     auto issue = [&](int64_t q) {
+        if (q == p.unissued) return;  // the wait on this stage runs out
         const int s = (int)(q % ST);
         const int64_t jt = q % p.ntiles;
         float *dst = stages + s * NC * TJ;
@@ -230,7 +232,8 @@ __global__ void __launch_bounds__(NT) jerk_kernel(const JerkParams p) {
                 const long long drain = p.timeout > kDefaultTimeoutCycles ? p.timeout
                                                                        : kDefaultTimeoutCycles;
                 for (int64_t r = q; r < nq && r < q + ST; ++r)
-                    mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
+                    if (r != p.unissued)
+                        mbar_wait_bounded(&full[r % ST], (uint32_t)((r / ST) & 1), drain);
             }
             __syncthreads();
             return;
@@ -308,6 +311,7 @@ int launch_jerk(const JerkJob &j) {
     p.pot = j.pot;
     p.status = reinterpret_cast<uint32_t *>(j.ws + j.L.status);
     p.timeout = j.timeout;
+    p.unissued = j.unissued;
     const bool guard = j.eps == 0.0;
     const int threads = 256;
     const int64_t pblocks = std::min<int64_t>(cdiv(j.L.Np, threads), 8192);

@@ -119,6 +119,8 @@ extern "C" int nb_forces_noalloc(const double *pos, const double *mass, int64_t 
     j.pos = pos;
     j.mass = mass;
     j.N = N;
+    j.i0 = 0;
+    j.ni = N;
     j.eps = eps;
     j.G = o->G;
     j.acc = acc;
@@ -126,6 +128,7 @@ extern "C" int nb_forces_noalloc(const double *pos, const double *mass, int64_t 
     j.precision = o->precision;
     j.split = positions_split(o);
     j.timeout = o->timeout_cycles > 0 ? (long long)o->timeout_cycles : kDefaultTimeoutCycles;
+    j.unissued = o->test_unissued_stage > 0 ? (int64_t)o->test_unissued_stage - 1 : -1;
     j.stream = st;
     j.ws = ws;
     return launch_force(j);

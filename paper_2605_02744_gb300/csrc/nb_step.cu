@@ -53,6 +53,27 @@ int launch_kick_drift_pack(double *pos, double *vel, const double *acc, const do
     return NB_OK;
 }
 
+__global__ void kick_drift_kernel(double *__restrict__ pos, double *__restrict__ vel,
+                                  const double *__restrict__ acc, int64_t n, double kick,
+                                  double drift) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = vel[t] + kick * acc[t];
+        vel[t] = v;
+        if (drift != 0.0) pos[t] = pos[t] + drift * v;
+    }
+}
+
+int launch_kick_drift(double *pos, double *vel, const double *acc, int64_t n, double kick,
+                      double drift, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>(cdiv(3 * n, threads), 8192);
+    kick_drift_kernel<<<(unsigned)blocks, threads, 0, st>>>(pos, vel, acc, n, kick, drift);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
 constexpr int kEnergyThreads = 256;
 constexpr int kEnergyMaxBlocks = 1024;
 

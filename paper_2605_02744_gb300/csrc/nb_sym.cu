@@ -60,6 +60,8 @@
 // mask per warp and item, from the Hilbert-sorted pack's boxes).
 #include <cuda_runtime.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -353,6 +355,281 @@ __global__ void __launch_bounds__(1024) sym_exponent_kernel(const double *__rest
     }
 }
 
+// ------------------------------------------------- j-pair pair kernel
+// The same decomposition with the roles of the packed halves swapped: a
+// lane holds 8 i-slots, each pre-broadcast as (x, x) pairs, and TWO
+// j-particles of a 64-slot j-set in the .x / .y halves.  Every FP32
+// operation of the pair term is then a packed f32x2 one -- no scalar j-side
+// FMAs, no per-step broadcast moves -- and one rotation step serves 16 pairs
+// for 16 shuffles.  The i-side sums are kept per j-stream (.x, .y) and
+// added when flushed.  8 warps per CTA (one CTA per SM) leave room for the
+// larger register state (8 warps of 8 i-slots, or 16 of 4).
+constexpr int JSJ = 64;             // slots per j-set (two per lane)
+constexpr int NJSJ = BI / JSJ;      // j-sets per block
+constexpr int KBJ = 2;              // j-sets per cross-warp reduction (128 slots)
+constexpr int FLJ = 2;              // j-sets per i-side flush (128 terms)
+constexpr int FL2J = 8;             // F64ACC: j-sets per flush of the FP32 middle sums
+static_assert(NJSJ == 32, "one 32-bit near mask per warp and item");
+static_assert(NJSJ / KBJ == US, "the stream-K units of the split");
+template <int NWJ>
+__host__ __device__ constexpr size_t red_bytes_j() { return 2 * KBJ * 2 * NWJ * 32 * sizeof(float4); }
+
+template <int IRJ>
+struct ISetJ {
+    float2 nx[IRJ], ny[IRJ], nz[IRJ];     // (-x_i.hi, -x_i.hi)
+    float nxl[IRJ], nyl[IRJ], nzl[IRJ];   // -x_i.lo
+    float2 m[IRJ];                        // (m_i, m_i)
+    float2 ax[IRJ], ay[IRJ], az[IRJ], ph[IRJ];  // per j-stream running sums
+};
+
+// One rotation step: the lane's 8 i-slots against its two current j.
+// B* accumulate +m_i r^-3 d and +m_i r^-1 for the two j (the j-side
+// acceleration is -B).  SELF: i-slots 2 self_h (.x) and 2 self_h + 1 (.y)
+// are the j-particles themselves (zero mass for the pair).
+template <int IRJ, bool NEAR, bool SYM, bool POT, bool SELF>
+__device__ __forceinline__ void stepj(ISetJ<IRJ> &S, const float2 e2, const float2 JX, const float2 JY,
+                                      const float2 JZ, const float2 JM, const float2 JXL,
+                                      const float2 JYL, const float2 JZL, float2 &BX, float2 &BY,
+                                      float2 &BZ, float2 &BP, int self_h) {
+#pragma unroll
+    for (int k = 0; k < IRJ; ++k) {
+        float2 dx = add2(JX, S.nx[k]);
+        float2 dy = add2(JY, S.ny[k]);
+        float2 dz = add2(JZ, S.nz[k]);
+        if (NEAR) {
+            dx = add2(dx, add2(JXL, f2(S.nxl[k], S.nxl[k])));
+            dy = add2(dy, add2(JYL, f2(S.nyl[k], S.nyl[k])));
+            dz = add2(dz, add2(JZL, f2(S.nzl[k], S.nzl[k])));
+        }
+        float2 r2 = fma2(dx, dx, e2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        const float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 ri3 = mul2(mul2(ri, ri), ri);
+        float2 M = JM;
+        if (SELF) {
+            M.x = (k == 2 * self_h) ? 0.f : M.x;
+            M.y = (k == 2 * self_h + 1) ? 0.f : M.y;
+        }
+        const float2 sj = mul2(M, ri3);
+        S.ax[k] = fma2(sj, dx, S.ax[k]);
+        S.ay[k] = fma2(sj, dy, S.ay[k]);
+        S.az[k] = fma2(sj, dz, S.az[k]);
+        if (POT) S.ph[k] = fma2(M, ri, S.ph[k]);
+        if (SYM) {
+            const float2 si = mul2(S.m[k], ri3);
+            BX = fma2(si, dx, BX);
+            BY = fma2(si, dy, BY);
+            BZ = fma2(si, dz, BZ);
+            if (POT) BP = fma2(S.m[k], ri, BP);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return f2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// 32 steps over one 64-slot j-set (j[0..6]: slot l, j[7..13]: slot 32 + l);
+// b0 / b1: the j-side sums (-a, phi order as BX, BY, BZ, BP) of the two
+// j-particles, home again on their lane.
+template <int IRJ, bool NEAR, bool SYM, bool POT>
+__device__ __forceinline__ void rotate_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
+                                            float4 &b0, float4 &b1, int self_h) {
+    const int src = (threadIdx.x + 1) & 31;
+    float2 JX = f2(j[0], j[7]), JY = f2(j[1], j[8]), JZ = f2(j[2], j[9]), JM = f2(j[3], j[10]);
+    float2 JXL = f2(j[4], j[11]), JYL = f2(j[5], j[12]), JZL = f2(j[6], j[13]);
+    float2 BX = f2(0.f, 0.f), BY = BX, BZ = BX, BP = BX;
+    auto rotate = [&]() {
+        JX = shfl2(JX, src);
+        JY = shfl2(JY, src);
+        JZ = shfl2(JZ, src);
+        JM = shfl2(JM, src);
+        if (NEAR) {
+            JXL = shfl2(JXL, src);
+            JYL = shfl2(JYL, src);
+            JZL = shfl2(JZL, src);
+        }
+        if (SYM) {
+            BX = shfl2(BX, src);
+            BY = shfl2(BY, src);
+            BZ = shfl2(BZ, src);
+            if (POT) BP = shfl2(BP, src);
+        }
+    };
+    int s0 = 0;
+    if (self_h >= 0) {
+        stepj<IRJ, NEAR, SYM, POT, true>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP, self_h);
+        rotate();
+        s0 = 1;
+    }
+#pragma unroll 2
+    for (int st = s0; st < 32; ++st) {
+        stepj<IRJ, NEAR, SYM, POT, false>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP, -1);
+        rotate();
+    }
+    b0 = make_float4(BX.x, BY.x, BZ.x, BP.x);
+    b1 = make_float4(BX.y, BY.y, BZ.y, BP.y);
+}
+
+template <int IRJ, int MODE, bool SYM, bool POT>
+__device__ __forceinline__ void run_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
+                                         bool near, float4 &b0, float4 &b1, int self_h) {
+    if (MODE == 1 || (MODE == 2 && near))
+        rotate_setj<IRJ, true, SYM, POT>(S, e2, j, b0, b1, self_h);
+    else
+        rotate_setj<IRJ, false, SYM, POT>(S, e2, j, b0, b1, self_h);
+}
+
+__device__ __forceinline__ void load_jp(const SymParams &p, int64_t s, float (&j)[14]) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        j[a] = __ldg(p.soa + a * p.Np + s);
+        j[7 + a] = __ldg(p.soa + a * p.Np + s + 32);
+    }
+}
+
+template <int NWJ, int IRJ, int POL, int MODE, bool POT>
+__global__ void __launch_bounds__(NWJ * 32, 1) force_symj_kernel(const SymParams p) {
+    static_assert(NWJ * 32 * IRJ == BI, "block");
+    constexpr int SNTJ = NWJ * 32;
+    constexpr int HW = IRJ / 2;  // j-sets per warp i-set
+    constexpr size_t kRedBytesJ = red_bytes_j<NWJ>();
+    extern __shared__ __align__(16) unsigned char smemj[];
+    float4 *red = reinterpret_cast<float4 *>(smemj);  // [2][KBJ][2 halves][NWJ][32]
+    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smemj + kRedBytesJ);  // [IRJ * 4][SNTJ]
+    constexpr bool MID = POL == NB_PREC_F64ACC;
+    float *mid = reinterpret_cast<float *>(smemj + kRedBytesJ + 4 * IRJ * SNTJ * sizeof(Acc<POL>));
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    const int64_t c = blockIdx.x;
+    int64_t u = __ldg(p.lo + c);
+    const int64_t u_end = __ldg(p.lo + c + 1);
+    if (u >= u_end) return;
+    const int F = __ldg(p.fx_exp);
+    const int64_t t0 = u / US;
+    int64_t I = 0;
+    while (row_start(I + 1, p.nb) <= t0) ++I;
+    int64_t J = I + (t0 - row_start(I, p.nb));
+    const float2 e2 = f2(p.eps2, p.eps2);
+    ISetJ<IRJ> S;
+    int half = 0;
+    bool row_open = false;
+    while (u < u_end) {
+        const int qa = (int)(u % US) * KBJ;
+        const int64_t item_end = (u / US + 1) * US;
+        const int64_t seg_end = item_end < u_end ? item_end : u_end;
+        const int qb = qa + (int)(seg_end - u) * KBJ;
+        const int64_t ib = I * BI + w * (32 * IRJ);  // this warp's i-set
+        if (!row_open) {
+#pragma unroll
+            for (int k = 0; k < IRJ; ++k) {
+                const int64_t sl = ib + 32 * k + l;
+                const float x = __ldg(p.soa + sl), y = __ldg(p.soa + p.Np + sl),
+                            z = __ldg(p.soa + 2 * p.Np + sl), m = __ldg(p.soa + 3 * p.Np + sl);
+                S.nx[k] = f2(-x, -x);
+                S.ny[k] = f2(-y, -y);
+                S.nz[k] = f2(-z, -z);
+                S.m[k] = f2(m, m);
+                S.nxl[k] = -__ldg(p.soa + 4 * p.Np + sl);
+                S.nyl[k] = -__ldg(p.soa + 5 * p.Np + sl);
+                S.nzl[k] = -__ldg(p.soa + 6 * p.Np + sl);
+                S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 4 * IRJ; ++v) {
+                tot[v * SNTJ + tid].zero();
+                if (MID) mid[v * SNTJ + tid] = 0.f;
+            }
+            row_open = true;
+        }
+        const bool sym = J != I;
+        const int64_t jb = J * BI;
+        unsigned near = 0u;
+        if (MODE == 2) {
+            float wb[7], tb[7];
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                wb[a] = __ldg(p.wbox + (ib / (32 * IRJ)) * 8 + a);
+                tb[a] = __ldg(p.jbox + (jb / JSJ + l) * 8 + a);
+            }
+            near = __ballot_sync(0xffffffffu, boxes_near(wb, tb, p.gamma));
+        }
+        float jn[14];
+        load_jp(p, jb + qa * JSJ + l, jn);
+        for (int q = qa; q < qb; ++q) {
+            float jc[14];
+#pragma unroll
+            for (int a = 0; a < 14; ++a) jc[a] = jn[a];
+            if (q + 1 < qb) load_jp(p, jb + (q + 1) * JSJ + l, jn);
+            const bool nq = (near >> q) & 1u;
+            float4 b0, b1;
+            if (sym) {
+                run_setj<IRJ, MODE, true, POT>(S, e2, jc, nq, b0, b1, -1);
+                float4 *r = red + (((half * KBJ + (q % KBJ)) * 2) * NWJ + w) * 32 + l;
+                r[0] = b0;
+                r[NWJ * 32] = b1;
+            } else {
+                // the warp's own slots are j-sets HW w .. HW w + HW - 1 of the block
+                run_setj<IRJ, MODE, false, POT>(S, e2, jc, nq, b0, b1,
+                                                q / HW == w ? q % HW : -1);
+            }
+            if ((q + 1) % FLJ == 0 || q + 1 == qb) {
+#pragma unroll
+                for (int k = 0; k < IRJ; ++k) {
+                    const float2 v4[4] = {S.ax[k], S.ay[k], S.az[k], S.ph[k]};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int v = (k * 4 + e) * SNTJ + tid;
+                        const float val = v4[e].x + v4[e].y;
+                        if (MID)
+                            mid[v] += val;
+                        else
+                            tot[v].add(val);
+                    }
+                    S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
+                }
+                if (MID && ((q + 1) % FL2J == 0 || q + 1 == qb)) {
+#pragma unroll
+                    for (int v = 0; v < 4 * IRJ; ++v) {
+                        tot[v * SNTJ + tid].add(mid[v * SNTJ + tid]);
+                        mid[v * SNTJ + tid] = 0.f;
+                    }
+                }
+            }
+            if (sym && (q + 1) % KBJ == 0) {
+                __syncthreads();
+                for (int v = tid; v < KBJ * JSJ * 4; v += SNTJ) {
+                    const int e = v & 3, js = (v >> 2) & (JSJ - 1), qq = v >> 8;
+                    const float *r = reinterpret_cast<const float *>(
+                                         red + (((half * KBJ + qq) * 2 + (js >> 5)) * NWJ) * 32 +
+                                         (js & 31)) + e;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int w2 = 0; w2 < NWJ; ++w2) sum += r[w2 * 32 * 4];
+                    if (POT || e < 3)
+                        add_fixed(p, e, jb + (q + 1 - KBJ + qq) * JSJ + js, e < 3 ? -sum : sum, F);
+                }
+                half ^= 1;
+            }
+        }
+        u = seg_end;
+        if ((J == p.nb - 1 && qb == NJSJ) || u == u_end) {
+#pragma unroll
+            for (int k = 0; k < IRJ; ++k) {
+                const int64_t slot = ib + 32 * k + l;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (POT || e < 3) add_fixed(p, e, slot, tot[(k * 4 + e) * SNTJ + tid].value(), F);
+            }
+            row_open = false;
+        }
+        if (qb == NJSJ && ++J == p.nb) {
+            ++I;
+            J = I;
+        }
+    }
+}
+
 // ------------------------------------------------------------- FP64 pairs
 // The same decomposition with FP64 arithmetic throughout (positions, pairs,
 // sums), for the FP64 policy: each unordered pair once, its j-side sums
@@ -543,8 +820,10 @@ __device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64
 }
 
 // One warp per item: the near/far decisions the pair kernel will take.
-template <int MODE>
+template <int MODE, int NWK, int JSET>
 __global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32_t *cost) {
+    constexpr int NJ = BI / JSET;  // j-sets per block
+    constexpr int WS = BI / NWK;   // i-slots per warp
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int l = threadIdx.x & 31;
     if (t >= p.T) return;  // whole warps
@@ -555,18 +834,19 @@ __global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32
     const uint32_t cf = sym ? kCostSymFar : kCostDiagFar;
     uint32_t c = 0;
     if (MODE != 2) {
-        c = (MODE == 1 ? cn : cf) * (NJS / 32) * SW;  // this lane's j-sets x the block's warps
+        c = (MODE == 1 ? cn : cf) * (NJ / 32) * NWK;  // this lane's j-sets x the block's warps
     } else {
-        constexpr int H = NJS / 32;  // j-sets of the block per lane
+        constexpr int H = NJ / 32;  // j-sets of the block per lane
         float tb[H][7];
 #pragma unroll
         for (int h = 0; h < H; ++h)
 #pragma unroll
-            for (int a = 0; a < 7; ++a) tb[h][a] = __ldg(p.jbox + (J * BI / JS + l + 32 * h) * 8 + a);
-        for (int w = 0; w < SW; ++w) {
+            for (int a = 0; a < 7; ++a)
+                tb[h][a] = __ldg(p.jbox + (J * BI / JSET + l + 32 * h) * 8 + a);
+        for (int w = 0; w < NWK; ++w) {
             float wb[7];
 #pragma unroll
-            for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + ((I * BI + w * 128) / 128) * 8 + a);
+            for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + ((I * BI + w * WS) / WS) * 8 + a);
 #pragma unroll
             for (int h = 0; h < H; ++h) c += boxes_near(wb, tb[h], p.gamma) ? cn : cf;
         }
@@ -646,9 +926,14 @@ int launch_pair(const SymParams &p, cudaStream_t st) {
 
 // Cost-weighted stream-K split of the items over the CTAs and the call's
 // fixed-point exponent: the kernels that run before the pair kernel.
-template <int MODE>
+// JPW: warps per CTA of the j-pair kernel (0: the 32 / 128 kernel).
+template <int MODE, int JPW = 0>
 int launch_split(const SymParams &p, const ForceJob &j, const SymLayout &y) {
-    sym_cost_kernel<MODE><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
+    if (JPW)
+        sym_cost_kernel<MODE, (JPW ? JPW : 1), JSJ>
+            <<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
+    else
+        sym_cost_kernel<MODE, SW, JS><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
     sym_scan_kernel<<<1, 1024, 0, j.stream>>>(y.cost, p.T, y.prefix);
     sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
         y.cost, y.prefix, p.T, p.ctas, y.lo);
@@ -667,8 +952,35 @@ int launch_fold(const SymParams &p, const ForceJob &j, const int *perm) {
     return NB_OK;
 }
 
+template <int NWJ, int IRJ, int POL, int MODE, bool POT>
+int launch_pairj(const SymParams &p, cudaStream_t st) {
+    auto kern = force_symj_kernel<NWJ, IRJ, POL, MODE, POT>;
+    const size_t smem = red_bytes_j<NWJ>() + 4 * BI * sizeof(Acc<POL>) +
+                        (POL == NB_PREC_F64ACC ? 4 * BI * sizeof(float) : 0);
+    const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
+    if (rc != NB_OK) return rc;
+    kernel_timer_begin(st);
+    kern<<<(unsigned)p.ctas, NWJ * 32, smem, st>>>(p);
+    kernel_timer_end(st);
+    count_launch();
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
 template <int POL, int MODE>
 int launch_sym_mode(const SymParams &p, const ForceJob &j, const SymLayout &y, const int *perm) {
+    if (sym_jpair() == 1) {
+        NB_TRY_SYM(launch_split<MODE, 8>(p, j, y));
+        NB_TRY_SYM(j.pot ? launch_pairj<8, 8, POL, MODE, true>(p, j.stream)
+                         : launch_pairj<8, 8, POL, MODE, false>(p, j.stream));
+        return launch_fold(p, j, perm);
+    }
+    if (sym_jpair() == 2) {
+        NB_TRY_SYM(launch_split<MODE, 16>(p, j, y));
+        NB_TRY_SYM(j.pot ? launch_pairj<16, 4, POL, MODE, true>(p, j.stream)
+                         : launch_pairj<16, 4, POL, MODE, false>(p, j.stream));
+        return launch_fold(p, j, perm);
+    }
     NB_TRY_SYM(launch_split<MODE>(p, j, y));
     NB_TRY_SYM(j.pot ? launch_pair<POL, MODE, true>(p, j.stream)
                      : launch_pair<POL, MODE, false>(p, j.stream));
@@ -703,6 +1015,14 @@ int launch_sym_pol(const SymParams &p, const ForceJob &j, const SymLayout &y, in
 }
 
 }  // namespace
+
+int sym_jpair() {
+    static const int v = [] {
+        const char *e = getenv("NB_SYM_JPAIR");
+        return (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+    }();
+    return v;
+}
 
 SymSizes sym_sizes(int64_t Np) {
     SymSizes z{};
