@@ -142,16 +142,16 @@ class ClockSampler:
 def _kernel_source_hash():
     """Hash of the pair kernel's source: the device code of nb_sym.cu (from
     its constants to the end of force_sym_kernel, host launch code excluded)
-    and the two device headers it includes."""
+    and the device headers it includes."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2605_02744_gb300", "csrc")
     h = hashlib.sha256()
     with open(os.path.join(csrc, "nb_sym.cu")) as fh:
         src = fh.read()
-    a = src.index("constexpr int SW = ")
+    a = src.index("constexpr int BI = 2048;")
     b = src.index("__global__ void __launch_bounds__(256) sym_fold_kernel(")
     h.update(src[a:b].encode())
-    for f in ("nb_sym_core.cuh", "nb_device.cuh"):
+    for f in ("nb_sym_core.cuh", "nb_device.cuh", "nb_fixed.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

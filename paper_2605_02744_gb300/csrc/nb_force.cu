@@ -518,10 +518,10 @@ int launch_force(const ForceJob &j) {
     char *sb = j.ws + j.L.sortbuf;
     if (j.sym && guard) return fail(NB_ERR_UNSUPPORTED, "symmetric pairs need eps > 0");
     if (adaptive) {
-        // boxes per 64 j-slots and per warp of i-slots (direct kernel), or per
-        // 32-slot j-set and 128-slot warp i-set (symmetric kernel)
-        const int tile_unit = j.sym ? (sym_jpair() ? 64 : 32) : 64;
-        const int block_unit = j.sym ? (sym_jpair() == 1 ? 256 : 128) : 32 * sh0.ipt;
+        // boxes per 64 j-slots and per warp of i-slots (direct kernel: 32 IR
+        // slots; symmetric FP32 kernel: 256 slots)
+        const int tile_unit = 64;
+        const int block_unit = j.sym ? 256 : 32 * sh0.ipt;
         int rc = launch_sorted_pack(j.pos, j.mass, j.N, j.L.Np, soa, sort_perm(sb, j.L),
                                     sort_keys(sb), sort_box6(sb, j.L), sort_tile_boxes(sb, j.L),
                                     tile_unit, sort_block_boxes(sb, j.L), block_unit,

@@ -214,10 +214,6 @@ struct SymLayout {
     unsigned long long *acc_fx;    // [4][2][Np]
 };
 SymLayout sym_layout(char *ws, const WsLayout &L);
-// Which symmetric kernel: 0 = 32-slot j-sets / 128-slot warp i-sets,
-// 1 = j-pair kernel with 8 warps of 256 i-slots, 2 = j-pair with 16 warps
-// of 128 (both with 64-slot j-sets).
-int sym_jpair();
 // Whether the symmetric-pair path is provisioned / taken for N particles in
 // B clusters under opts (nb_pairs; FP32-pair policies, single systems).
 bool sym_wanted(const nb_opts *opts, int64_t N, int32_t B);

@@ -10,36 +10,44 @@
 //
 // Decomposition.  The (padded) slots are cut into row blocks of 2048; the
 // work items are the block pairs (I, J) with J >= I, in row-major order,
-// cut into units of 4 j-sets and split over one persistent CTA per SM into
+// cut into units of 2 j-sets and split over one persistent CTA per SM into
 // contiguous ranges of equal estimated cost (stream-K: a range may start or
 // end inside an item).  The estimate counts FP32 operations per (warp,
 // j-set) from the same near/far box tests the pair kernel makes; three small
 // kernels compute it, scan it and cut the ranges.
-// A CTA keeps block I in registers: warp w holds the 128 slots
-// I*2048 + w*128 + [0, 128), lane l the four slots  + 32k + l  (k = 0..3,
-// two packed f32x2 pairs).  For every 32-slot j-set of block J each warp
-// loads one j-particle per lane and rotates the set through its lanes with
-// shuffles: at step s lane l holds j-slot (l + s) mod 32, so in 32 steps
-// every lane meets every j once, and the j-particle's own sums (a_j, phi_j)
-// travel with it and come home to lane l.
+// A CTA of 8 warps keeps block I in registers: warp w holds the 256 slots
+// I*2048 + w*256 + [0, 256), lane l the eight slots  + 32k + l  (k = 0..7),
+// each pre-broadcast as an (x, x) pair.  A j-set is 64 slots of block J;
+// lane l loads two of them, j-slots l and 32 + l, into the .x / .y halves
+// of packed f32x2 registers, so every FP32 operation of the pair term is a
+// packed one (one rotation step: 8 i-slots x 2 j = 16 pairs, 148 packed
+// FP32 instructions, 16 MUFU rsqrt, 16 shuffles).  The set rotates through
+// the lanes with shuffles: at step s lane l holds j-slots (l + s) mod 32 and
+// 32 + (l + s) mod 32, so in 32 steps every lane meets every j once, and the
+// j-particles' own sums (a_j, phi_j) travel with them and come home to lane
+// l.  Each step's eight j-side terms go into fresh registers and then into
+// the travelling sums with one add, so a strong close pair's term meets
+// ~47 later FP32 roundings within an item, not ~260.
 //
-//   * Off-diagonal items (I < J): both halves of every pair.  The 16 warps'
-//     j-side sums of 4 j-sets are added in warp order in shared memory (one
-//     barrier per 4 j-sets), giving the FP32 partial of the J-block
+//   * Off-diagonal items (I < J): both halves of every pair.  The 8 warps'
+//     j-side sums of 2 j-sets are added in warp order in shared memory (one
+//     barrier per 2 j-sets), giving the FP32 partial of the J-block
 //     particles from block I.
 //   * Diagonal items (I = J): the i-side only, over all ordered pairs of
-//     the block; the self pair (j-set 4w + k at rotation step 0 for lane
-//     slot k of warp w) gets a zero mass, so Eq. 1's j != i holds exactly.
+//     the block; the self pairs (j-set 4w + h at rotation step 0: i-slot 2h
+//     against the .x j, 2h + 1 against the .y j) get a zero mass, so Eq. 1's
+//     j != i holds exactly.
 //
-// The i-side FP32 register sums are folded into the accumulation policy
-// (FP32, Kahan or FP64; totals kept in shared memory) every 4 j-sets (128
-// terms per running sum; for F64ACC through an FP32 middle sum in shared
-// memory that goes into FP64 every 16 j-sets, FP64 adds being slow on this
-// part) over the CTA's segment of a row.  In Hilbert order a particle's
-// strongest, mutually cancelling terms (its spatial neighbours) arrive
-// together; with 16 j-sets per flush the FP32 running sums of central
-// particles of a log-normal Plummer sphere (N = 300001, eps = 1e-3) lost up
-// to 1e-5 of |a|, with 4 they stay at the 2e-6 of the unsorted order.
+// The i-side FP32 register sums, kept per j-stream (.x, .y), are folded into
+// the accumulation policy (FP32, Kahan or FP64; totals kept in shared
+// memory) every 2 j-sets (128 terms per particle; for F64ACC through an FP32
+// middle sum in shared memory that goes into FP64 every 8 j-sets, FP64 adds
+// being slow on this part) over the CTA's segment of a row.  In Hilbert
+// order a particle's strongest, mutually cancelling terms (its spatial
+// neighbours) arrive together; with 512 terms per flush the FP32 running
+// sums of central particles of a log-normal Plummer sphere (N = 300001,
+// eps = 1e-3) lost up to 1e-5 of |a|, with 128 they stay at the 2e-6 of the
+// unsorted order.
 //
 // Combining across CTAs.  Every particle's sum collects one j-side FP32
 // partial per block above it and one i-side total per CTA that worked on its
@@ -56,8 +64,13 @@
 //
 // Displacements: single floats, hi/lo pairs (x_j.hi - x_i.hi) +
 // (x_j.lo - x_i.lo), or adaptive: per (warp i-set, j-set) the hi/lo form
-// only when the bounding boxes are closer than gamma * max|x| (a 64-bit
-// mask per warp and item, from the Hilbert-sorted pack's boxes).
+// only when the bounding boxes are closer than gamma * max|x| (a 32-bit
+// mask per warp and item, from the Hilbert-sorted pack's boxes of 256 i-
+// and 64 j-slots).
+//
+// FP64 pairs (force_sym64_kernel) keep the first form of this kernel: 16
+// warps of 128 slots (4 per lane, doubles), 32-slot j-sets of one particle
+// per lane, scalar j-side sums.
 #include <cuda_runtime.h>
 
 #include <stdlib.h>
@@ -89,18 +102,28 @@ using namespace symcore;
         if (rc_ != NB_OK) return rc_;  \
     } while (0)
 
-constexpr int SW = 16;              // warps per CTA of the pair kernel
-constexpr int SNT = SW * 32;        // threads per CTA
-constexpr int CPS = 1;              // resident CTAs per SM
-constexpr int BI = SW * 32 * IR;    // slots per row block
-constexpr int NJS = BI / JS;        // j-sets per block
-constexpr int KB = 4;               // j-sets per cross-warp reduction
-constexpr int FL = 4;               // j-sets per i-side flush of the register sums
-constexpr int FL2 = 16;             // F64ACC: j-sets per flush of the FP32 middle sums
-constexpr int US = NJS / KB;        // stream-K units (KB j-sets) per item
+constexpr int BI = 2048;            // slots per row block
 static_assert(BI == kSymBlock, "row block size");
-static_assert(NJS % KB == 0 && NJS % FL2 == 0 && FL2 % FL == 0, "groups tile a block");
-constexpr size_t kRedBytes = 2 * KB * SW * 32 * sizeof(float4);
+constexpr int CPS = 1;              // resident CTAs per SM
+constexpr int US = 16;              // stream-K units per item (both kernels)
+// FP32 pairs (force_sym_kernel)
+constexpr int NW = 8;               // warps per CTA
+constexpr int NT = NW * 32;         // threads per CTA
+constexpr int IRP = 8;              // i-slots per lane
+constexpr int WS = 32 * IRP;        // i-slots per warp
+constexpr int JSP = 64;             // slots per j-set (two per lane)
+constexpr int NJSP = BI / JSP;      // j-sets per block: one 32-bit near mask
+constexpr int KBP = 2;              // j-sets per cross-warp reduction (128 slots)
+constexpr int FLP = 2;              // j-sets per i-side flush (128 terms)
+constexpr int FL2P = 8;             // F64ACC: j-sets per flush of the FP32 middle sums
+static_assert(NW * WS == BI && NJSP == 32 && NJSP / KBP == US, "FP32 kernel shape");
+constexpr size_t kRedBytes = 2 * KBP * 2 * NW * 32 * sizeof(float4);
+// FP64 pairs (force_sym64_kernel)
+constexpr int SW = 16;              // warps per CTA
+constexpr int SNT = SW * 32;        // threads per CTA
+constexpr int NJS = BI / JS;        // 32-slot j-sets per block
+constexpr int KB = 4;               // j-sets per cross-warp reduction
+static_assert(SW * 32 * IR == BI && NJS / KB == US, "FP64 kernel shape");
 
 struct SymParams {
     const float *soa;   // packed SoA [7][Np]
@@ -141,20 +164,182 @@ __device__ __forceinline__ void add_fixed(const SymParams &p, int e, int64_t s, 
     if (!fx::add_f32(w, w + p.Np, v, F)) dev::set_status(p.status, kStatusNonFinite);
 }
 
-__device__ __forceinline__ void load_j(const SymParams &p, int64_t s, float (&j)[7]) {
+// ------------------------------------------------------------- FP32 pairs
+// i-side state of one lane: 8 slots as broadcast pairs, their running sums
+// per j-stream (.x / .y).
+template <int IRJ>
+struct ISetJ {
+    float2 nx[IRJ], ny[IRJ], nz[IRJ];     // (-x_i.hi, -x_i.hi)
+    float nxl[IRJ], nyl[IRJ], nzl[IRJ];   // -x_i.lo
+    float2 m[IRJ];                        // (m_i, m_i)
+    float2 ax[IRJ], ay[IRJ], az[IRJ], ph[IRJ];  // per j-stream running sums
+};
+
+// One rotation step: the lane's i-slots against its two current j.  B*
+// receive +m_i r^-3 d and +m_i r^-1 for the two j (the j-side acceleration
+// is -B): the step's terms are summed into fresh registers first and added
+// to the travelling sums once, so a j-particle's FP32 sum over an item takes
+// 32 adds per j-set pass instead of 32 x IRJ (a strong close pair's term
+// then meets ~47 later roundings, not ~260).  SELF: i-slots 2 self_h (.x)
+// and 2 self_h + 1 (.y) are the j-particles themselves (zero mass).
+// A (lo, lo) pair of this thread's i-slots from shared memory, read at
+// every use (kept out of registers: only near j-sets need it).
+__device__ __forceinline__ float2 lds_pair(const float2 *q) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(dev::smem_addr(q)));
+    return v;
+}
+
+// LOSM: the i-slots' -x.lo values come as broadcast pairs from shared
+// memory (lo2[(c IRJ + k) stride]) instead of registers.
+template <int IRJ, bool NEAR, bool SYM, bool POT, bool SELF, bool LOSM>
+__device__ __forceinline__ void stepj(ISetJ<IRJ> &S, const float2 e2, const float2 JX, const float2 JY,
+                                      const float2 JZ, const float2 JM, const float2 JXL,
+                                      const float2 JYL, const float2 JZL, float2 &BX, float2 &BY,
+                                      float2 &BZ, float2 &BP, int self_h, const float2 *lo2,
+                                      int stride) {
+    float2 TX, TY, TZ, TP = f2(0.f, 0.f);  // this step's j-side terms
 #pragma unroll
-    for (int a = 0; a < 7; ++a) j[a] = __ldg(p.soa + a * p.Np + s);
+    for (int k = 0; k < IRJ; ++k) {
+        float2 dx = add2(JX, S.nx[k]);
+        float2 dy = add2(JY, S.ny[k]);
+        float2 dz = add2(JZ, S.nz[k]);
+        if (NEAR) {
+            if (LOSM) {
+                dx = add2(dx, add2(JXL, lds_pair(lo2 + (0 * IRJ + k) * stride)));
+                dy = add2(dy, add2(JYL, lds_pair(lo2 + (1 * IRJ + k) * stride)));
+                dz = add2(dz, add2(JZL, lds_pair(lo2 + (2 * IRJ + k) * stride)));
+            } else {
+                dx = add2(dx, add2(JXL, f2(S.nxl[k], S.nxl[k])));
+                dy = add2(dy, add2(JYL, f2(S.nyl[k], S.nyl[k])));
+                dz = add2(dz, add2(JZL, f2(S.nzl[k], S.nzl[k])));
+            }
+        }
+        float2 r2 = fma2(dx, dx, e2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        const float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 ri3 = mul2(mul2(ri, ri), ri);
+        float2 M = JM;
+        if (SELF) {
+            M.x = (k == 2 * self_h) ? 0.f : M.x;
+            M.y = (k == 2 * self_h + 1) ? 0.f : M.y;
+        }
+        const float2 sj = mul2(M, ri3);
+        S.ax[k] = fma2(sj, dx, S.ax[k]);
+        S.ay[k] = fma2(sj, dy, S.ay[k]);
+        S.az[k] = fma2(sj, dz, S.az[k]);
+        if (POT) S.ph[k] = fma2(M, ri, S.ph[k]);
+        if (SYM) {
+            const float2 si = mul2(S.m[k], ri3);
+            if (k == 0) {
+                TX = mul2(si, dx);
+                TY = mul2(si, dy);
+                TZ = mul2(si, dz);
+                if (POT) TP = mul2(S.m[k], ri);
+            } else {
+                TX = fma2(si, dx, TX);
+                TY = fma2(si, dy, TY);
+                TZ = fma2(si, dz, TZ);
+                if (POT) TP = fma2(S.m[k], ri, TP);
+            }
+        }
+    }
+    if (SYM) {
+        BX = add2(BX, TX);
+        BY = add2(BY, TY);
+        BZ = add2(BZ, TZ);
+        if (POT) BP = add2(BP, TP);
+    }
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return f2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// 32 steps over one 64-slot j-set (j[0..6]: slot l, j[7..13]: slot 32 + l);
+// b0 / b1: the j-side sums (-a, phi order as BX, BY, BZ, BP) of the two
+// j-particles, home again on their lane.
+template <int IRJ, bool NEAR, bool SYM, bool POT, bool LOSM>
+__device__ __forceinline__ void rotate_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
+                                            float4 &b0, float4 &b1, int self_h, const float2 *lo2,
+                                            int stride) {
+    const int src = (threadIdx.x + 1) & 31;
+    float2 JX = f2(j[0], j[7]), JY = f2(j[1], j[8]), JZ = f2(j[2], j[9]), JM = f2(j[3], j[10]);
+    float2 JXL = f2(j[4], j[11]), JYL = f2(j[5], j[12]), JZL = f2(j[6], j[13]);
+    float2 BX = f2(0.f, 0.f), BY = BX, BZ = BX, BP = BX;
+    auto rotate = [&]() {
+        JX = shfl2(JX, src);
+        JY = shfl2(JY, src);
+        JZ = shfl2(JZ, src);
+        JM = shfl2(JM, src);
+        if (NEAR) {
+            JXL = shfl2(JXL, src);
+            JYL = shfl2(JYL, src);
+            JZL = shfl2(JZL, src);
+        }
+        if (SYM) {
+            BX = shfl2(BX, src);
+            BY = shfl2(BY, src);
+            BZ = shfl2(BZ, src);
+            if (POT) BP = shfl2(BP, src);
+        }
+    };
+    int s0 = 0;
+    if (self_h >= 0) {
+        stepj<IRJ, NEAR, SYM, POT, true, LOSM>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP,
+                                               self_h, lo2, stride);
+        rotate();
+        s0 = 1;
+    }
+#pragma unroll 2
+    for (int st = s0; st < 32; ++st) {
+        stepj<IRJ, NEAR, SYM, POT, false, LOSM>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP,
+                                                -1, lo2, stride);
+        rotate();
+    }
+    b0 = make_float4(BX.x, BY.x, BZ.x, BP.x);
+    b1 = make_float4(BX.y, BY.y, BZ.y, BP.y);
+}
+
+template <int IRJ, int MODE, bool SYM, bool POT, bool LOSM>
+__device__ __forceinline__ void run_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
+                                         bool near, float4 &b0, float4 &b1, int self_h,
+                                         const float2 *lo2, int stride) {
+    if (MODE == 1 || (MODE == 2 && near))
+        rotate_setj<IRJ, true, SYM, POT, LOSM>(S, e2, j, b0, b1, self_h, lo2, stride);
+    else
+        rotate_setj<IRJ, false, SYM, POT, LOSM>(S, e2, j, b0, b1, self_h, lo2, stride);
+}
+
+__device__ __forceinline__ void load_jp(const SymParams &p, int64_t s, float (&j)[14]) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        j[a] = __ldg(p.soa + a * p.Np + s);
+        j[7 + a] = __ldg(p.soa + a * p.Np + s + 32);
+    }
 }
 
 // MODE: 0 single-float displacement, 1 hi/lo, 2 adaptive.  POT: the
-// potential sums too (the caller wants phi).
+// potential sums too (the caller wants phi).  The i-slots' lo parts stay in
+// registers for MODE 1 (every j-set is near) and come from shared memory
+// for MODE 2 (only near j-sets use them; 245 of 255 registers are taken).
 template <int POL, int MODE, bool POT>
-__global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4 *red = reinterpret_cast<float4 *>(smem);                   // [2][KB][SW][32]
-    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smem + kRedBytes);   // [16][SNT]
+__global__ void __launch_bounds__(NT, CPS) force_sym_kernel(const SymParams p) {
+    constexpr int NWJ = NW, IRJ = IRP, SNTJ = NT;
+    constexpr bool LOSM = MODE == 2;
+    constexpr int HW = IRJ / 2;  // j-sets per warp i-set
+    constexpr size_t kRedBytesJ = kRedBytes;
+    extern __shared__ __align__(16) unsigned char smemj[];
+    float4 *red = reinterpret_cast<float4 *>(smemj);  // [2][KBP][2 halves][NWJ][32]
+    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smemj + kRedBytesJ);  // [IRJ * 4][SNTJ]
     constexpr bool MID = POL == NB_PREC_F64ACC;
-    float *mid = reinterpret_cast<float *>(smem + kRedBytes + 16 * SNT * sizeof(Acc<POL>));
+    float *mid = reinterpret_cast<float *>(smemj + kRedBytesJ + 4 * IRJ * SNTJ * sizeof(Acc<POL>));
+    // LOSM: (-x.lo, -x.lo) pairs [3][IRJ][SNTJ] after the F64ACC middle sums
+    float2 *lo2 = reinterpret_cast<float2 *>(smemj + kRedBytesJ +
+                                             4 * IRJ * SNTJ * sizeof(Acc<POL>) +
+                                             (MID ? 4 * IRJ * SNTJ * sizeof(float) : 0)) +
+                  threadIdx.x;
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     const int64_t c = blockIdx.x;
     int64_t u = __ldg(p.lo + c);
@@ -166,125 +351,129 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym_kernel(const SymParams p) 
     while (row_start(I + 1, p.nb) <= t0) ++I;
     int64_t J = I + (t0 - row_start(I, p.nb));
     const float2 e2 = f2(p.eps2, p.eps2);
-    ISet S;
+    ISetJ<IRJ> S;
     int half = 0;
     bool row_open = false;
     while (u < u_end) {
-        // this CTA's j-sets [qa, qb) of item (I, J)
-        const int qa = (int)(u % US) * KB;
+        const int qa = (int)(u % US) * KBP;
         const int64_t item_end = (u / US + 1) * US;
         const int64_t seg_end = item_end < u_end ? item_end : u_end;
-        const int qb = qa + (int)(seg_end - u) * KB;
-        const int64_t ib = I * BI + w * 128;  // this warp's i-set
+        const int qb = qa + (int)(seg_end - u) * KBP;
+        const int64_t ib = I * BI + w * (32 * IRJ);  // this warp's i-set
         if (!row_open) {
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                float v[2][7];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) load_j(p, ib + 32 * (2 * g + h) + l, v[h]);
-                S.nx[g] = f2(-v[0][0], -v[1][0]);
-                S.ny[g] = f2(-v[0][1], -v[1][1]);
-                S.nz[g] = f2(-v[0][2], -v[1][2]);
-                S.m[g] = f2(v[0][3], v[1][3]);
-                S.nm[g] = f2(-v[0][3], -v[1][3]);
-                S.nxl[g] = f2(-v[0][4], -v[1][4]);
-                S.nyl[g] = f2(-v[0][5], -v[1][5]);
-                S.nzl[g] = f2(-v[0][6], -v[1][6]);
-                S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+            for (int k = 0; k < IRJ; ++k) {
+                const int64_t sl = ib + 32 * k + l;
+                const float x = __ldg(p.soa + sl), y = __ldg(p.soa + p.Np + sl),
+                            z = __ldg(p.soa + 2 * p.Np + sl), m = __ldg(p.soa + 3 * p.Np + sl);
+                S.nx[k] = f2(-x, -x);
+                S.ny[k] = f2(-y, -y);
+                S.nz[k] = f2(-z, -z);
+                S.m[k] = f2(m, m);
+                const float xl = __ldg(p.soa + 4 * p.Np + sl), yl = __ldg(p.soa + 5 * p.Np + sl),
+                            zl = __ldg(p.soa + 6 * p.Np + sl);
+                if (LOSM) {
+                    if (MODE != 0) {
+                        lo2[(0 * IRJ + k) * SNTJ] = f2(-xl, -xl);
+                        lo2[(1 * IRJ + k) * SNTJ] = f2(-yl, -yl);
+                        lo2[(2 * IRJ + k) * SNTJ] = f2(-zl, -zl);
+                    }
+                } else {
+                    S.nxl[k] = -xl;
+                    S.nyl[k] = -yl;
+                    S.nzl[k] = -zl;
+                }
+                S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
             }
 #pragma unroll
-            for (int v = 0; v < 16; ++v) {
-                tot[v * SNT + tid].zero();
-                if (MID) mid[v * SNT + tid] = 0.f;
+            for (int v = 0; v < 4 * IRJ; ++v) {
+                tot[v * SNTJ + tid].zero();
+                if (MID) mid[v * SNTJ + tid] = 0.f;
             }
             row_open = true;
         }
         const bool sym = J != I;
         const int64_t jb = J * BI;
-        // near mask of this warp's i-set against the block's 64 j-sets
-        unsigned long long near = 0ull;
+        unsigned near = 0u;
         if (MODE == 2) {
-            float wb[7];
+            float wb[7], tb[7];
 #pragma unroll
-            for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + (ib / 128) * 8 + a);
-            static_assert(NJS == 32 || NJS == 64, "one or two 32-bit ballots per block");
-#pragma unroll
-            for (int h = 0; h < NJS / 32; ++h) {
-                float tb[7];
-#pragma unroll
-                for (int a = 0; a < 7; ++a) tb[a] = __ldg(p.jbox + (jb / JS + l + 32 * h) * 8 + a);
-                const unsigned m = __ballot_sync(0xffffffffu, boxes_near(wb, tb, p.gamma));
-                near |= (unsigned long long)m << (32 * h);
+            for (int a = 0; a < 7; ++a) {
+                wb[a] = __ldg(p.wbox + (ib / (32 * IRJ)) * 8 + a);
+                tb[a] = __ldg(p.jbox + (jb / JSP + l) * 8 + a);
             }
+            near = __ballot_sync(0xffffffffu, boxes_near(wb, tb, p.gamma));
         }
-        float jn[7];
-        load_j(p, jb + qa * JS + l, jn);
+        float jn[14];
+        load_jp(p, jb + qa * JSP + l, jn);
         for (int q = qa; q < qb; ++q) {
-            float jc[7];
+            float jc[14];
 #pragma unroll
-            for (int a = 0; a < 7; ++a) jc[a] = jn[a];
-            if (q + 1 < qb) load_j(p, jb + (q + 1) * JS + l, jn);
-            const bool nq = (near >> q) & 1ull;
-            float4 b;
+            for (int a = 0; a < 14; ++a) jc[a] = jn[a];
+            if (q + 1 < qb) load_jp(p, jb + (q + 1) * JSP + l, jn);
+            const bool nq = (near >> q) & 1u;
+            float4 b0, b1;
             if (sym) {
-                run_set<MODE, true, POT>(S, e2, jc, nq, b, -1);
-                red[((half * KB + (q % KB)) * SW + w) * 32 + l] = b;
+                run_setj<IRJ, MODE, true, POT, LOSM>(S, e2, jc, nq, b0, b1, -1, lo2, SNTJ);
+                float4 *r = red + (((half * KBP + (q % KBP)) * 2) * NWJ + w) * 32 + l;
+                r[0] = b0;
+                r[NWJ * 32] = b1;
             } else {
-                run_set<MODE, false, POT>(S, e2, jc, nq, b, (q >> 2) == w ? (q & 3) : -1);
+                // the warp's own slots are j-sets HW w .. HW w + HW - 1 of the block
+                run_setj<IRJ, MODE, false, POT, LOSM>(S, e2, jc, nq, b0, b1,
+                                                  q / HW == w ? q % HW : -1, lo2, SNTJ);
             }
-            if ((q + 1) % FL == 0 || q + 1 == qb) {
+            if ((q + 1) % FLP == 0 || q + 1 == qb) {
 #pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const float2 v4[4] = {S.ax[g], S.ay[g], S.az[g], S.ph[g]};
+                for (int k = 0; k < IRJ; ++k) {
+                    const float2 v4[4] = {S.ax[k], S.ay[k], S.az[k], S.ph[k]};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int v0 = ((2 * g) * 4 + e) * SNT + tid;
-                        const int v1 = ((2 * g + 1) * 4 + e) * SNT + tid;
-                        if (MID) {
-                            mid[v0] += v4[e].x;
-                            mid[v1] += v4[e].y;
-                        } else {
-                            tot[v0].add(v4[e].x);
-                            tot[v1].add(v4[e].y);
-                        }
+                        const int v = (k * 4 + e) * SNTJ + tid;
+                        const float val = v4[e].x + v4[e].y;
+                        if (MID)
+                            mid[v] += val;
+                        else
+                            tot[v].add(val);
                     }
-                    S.ax[g] = S.ay[g] = S.az[g] = S.ph[g] = f2(0.f, 0.f);
+                    S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
                 }
-                if (MID && ((q + 1) % FL2 == 0 || q + 1 == qb)) {
+                if (MID && ((q + 1) % FL2P == 0 || q + 1 == qb)) {
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) {
-                        tot[v * SNT + tid].add(mid[v * SNT + tid]);
-                        mid[v * SNT + tid] = 0.f;
+                    for (int v = 0; v < 4 * IRJ; ++v) {
+                        tot[v * SNTJ + tid].add(mid[v * SNTJ + tid]);
+                        mid[v * SNTJ + tid] = 0.f;
                     }
                 }
             }
-            if (sym && (q + 1) % KB == 0) {
+            if (sym && (q + 1) % KBP == 0) {
                 __syncthreads();
-                for (int v = tid; v < KB * JS * 4; v += SNT) {
-                    const int qq = v >> 7, ll = (v >> 2) & 31, e = v & 3;
-                    const float *r = reinterpret_cast<const float *>(red) +
-                                     ((half * KB + qq) * SW * 32 + ll) * 4 + e;
-                    float s = 0.f;
+                for (int v = tid; v < KBP * JSP * 4; v += SNTJ) {
+                    const int e = v & 3, js = (v >> 2) & (JSP - 1), qq = v >> 8;
+                    const float *r = reinterpret_cast<const float *>(
+                                         red + (((half * KBP + qq) * 2 + (js >> 5)) * NWJ) * 32 +
+                                         (js & 31)) + e;
+                    float sum = 0.f;
 #pragma unroll
-                    for (int w2 = 0; w2 < SW; ++w2) s += r[w2 * 32 * 4];
-                    if (POT || e < 3) add_fixed(p, e, jb + (q + 1 - KB + qq) * JS + ll, s, F);
+                    for (int w2 = 0; w2 < NWJ; ++w2) sum += r[w2 * 32 * 4];
+                    if (POT || e < 3)
+                        add_fixed(p, e, jb + (q + 1 - KBP + qq) * JSP + js, e < 3 ? -sum : sum, F);
                 }
                 half ^= 1;
             }
         }
         u = seg_end;
-        if ((J == p.nb - 1 && qb == NJS) || u == u_end) {
-            // row segment done: the policy totals into the fixed-point sums
+        if ((J == p.nb - 1 && qb == NJSP) || u == u_end) {
 #pragma unroll
-            for (int kk = 0; kk < IR; ++kk) {
-                const int64_t slot = I * BI + w * 128 + 32 * kk + l;
+            for (int k = 0; k < IRJ; ++k) {
+                const int64_t slot = ib + 32 * k + l;
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (POT || e < 3) add_fixed(p, e, slot, tot[(kk * 4 + e) * SNT + tid].value(), F);
+                    if (POT || e < 3) add_fixed(p, e, slot, tot[(k * 4 + e) * SNTJ + tid].value(), F);
             }
             row_open = false;
         }
-        if (qb == NJS && ++J == p.nb) {
+        if (qb == NJSP && ++J == p.nb) {
             ++I;
             J = I;
         }
@@ -351,281 +540,6 @@ __global__ void __launch_bounds__(1024) sym_exponent_kernel(const double *__rest
         if (threadIdx.x == 0) {
             const double per = fmax(0.3849002 / (eps * eps), 1.0 / eps);
             *F = fx::exponent_for(1.02 * (double)N * m * per);
-        }
-    }
-}
-
-// ------------------------------------------------- j-pair pair kernel
-// The same decomposition with the roles of the packed halves swapped: a
-// lane holds 8 i-slots, each pre-broadcast as (x, x) pairs, and TWO
-// j-particles of a 64-slot j-set in the .x / .y halves.  Every FP32
-// operation of the pair term is then a packed f32x2 one -- no scalar j-side
-// FMAs, no per-step broadcast moves -- and one rotation step serves 16 pairs
-// for 16 shuffles.  The i-side sums are kept per j-stream (.x, .y) and
-// added when flushed.  8 warps per CTA (one CTA per SM) leave room for the
-// larger register state (8 warps of 8 i-slots, or 16 of 4).
-constexpr int JSJ = 64;             // slots per j-set (two per lane)
-constexpr int NJSJ = BI / JSJ;      // j-sets per block
-constexpr int KBJ = 2;              // j-sets per cross-warp reduction (128 slots)
-constexpr int FLJ = 2;              // j-sets per i-side flush (128 terms)
-constexpr int FL2J = 8;             // F64ACC: j-sets per flush of the FP32 middle sums
-static_assert(NJSJ == 32, "one 32-bit near mask per warp and item");
-static_assert(NJSJ / KBJ == US, "the stream-K units of the split");
-template <int NWJ>
-__host__ __device__ constexpr size_t red_bytes_j() { return 2 * KBJ * 2 * NWJ * 32 * sizeof(float4); }
-
-template <int IRJ>
-struct ISetJ {
-    float2 nx[IRJ], ny[IRJ], nz[IRJ];     // (-x_i.hi, -x_i.hi)
-    float nxl[IRJ], nyl[IRJ], nzl[IRJ];   // -x_i.lo
-    float2 m[IRJ];                        // (m_i, m_i)
-    float2 ax[IRJ], ay[IRJ], az[IRJ], ph[IRJ];  // per j-stream running sums
-};
-
-// One rotation step: the lane's 8 i-slots against its two current j.
-// B* accumulate +m_i r^-3 d and +m_i r^-1 for the two j (the j-side
-// acceleration is -B).  SELF: i-slots 2 self_h (.x) and 2 self_h + 1 (.y)
-// are the j-particles themselves (zero mass for the pair).
-template <int IRJ, bool NEAR, bool SYM, bool POT, bool SELF>
-__device__ __forceinline__ void stepj(ISetJ<IRJ> &S, const float2 e2, const float2 JX, const float2 JY,
-                                      const float2 JZ, const float2 JM, const float2 JXL,
-                                      const float2 JYL, const float2 JZL, float2 &BX, float2 &BY,
-                                      float2 &BZ, float2 &BP, int self_h) {
-#pragma unroll
-    for (int k = 0; k < IRJ; ++k) {
-        float2 dx = add2(JX, S.nx[k]);
-        float2 dy = add2(JY, S.ny[k]);
-        float2 dz = add2(JZ, S.nz[k]);
-        if (NEAR) {
-            dx = add2(dx, add2(JXL, f2(S.nxl[k], S.nxl[k])));
-            dy = add2(dy, add2(JYL, f2(S.nyl[k], S.nyl[k])));
-            dz = add2(dz, add2(JZL, f2(S.nzl[k], S.nzl[k])));
-        }
-        float2 r2 = fma2(dx, dx, e2);
-        r2 = fma2(dy, dy, r2);
-        r2 = fma2(dz, dz, r2);
-        const float2 ri = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        const float2 ri3 = mul2(mul2(ri, ri), ri);
-        float2 M = JM;
-        if (SELF) {
-            M.x = (k == 2 * self_h) ? 0.f : M.x;
-            M.y = (k == 2 * self_h + 1) ? 0.f : M.y;
-        }
-        const float2 sj = mul2(M, ri3);
-        S.ax[k] = fma2(sj, dx, S.ax[k]);
-        S.ay[k] = fma2(sj, dy, S.ay[k]);
-        S.az[k] = fma2(sj, dz, S.az[k]);
-        if (POT) S.ph[k] = fma2(M, ri, S.ph[k]);
-        if (SYM) {
-            const float2 si = mul2(S.m[k], ri3);
-            BX = fma2(si, dx, BX);
-            BY = fma2(si, dy, BY);
-            BZ = fma2(si, dz, BZ);
-            if (POT) BP = fma2(S.m[k], ri, BP);
-        }
-    }
-}
-
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return f2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-
-// 32 steps over one 64-slot j-set (j[0..6]: slot l, j[7..13]: slot 32 + l);
-// b0 / b1: the j-side sums (-a, phi order as BX, BY, BZ, BP) of the two
-// j-particles, home again on their lane.
-template <int IRJ, bool NEAR, bool SYM, bool POT>
-__device__ __forceinline__ void rotate_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
-                                            float4 &b0, float4 &b1, int self_h) {
-    const int src = (threadIdx.x + 1) & 31;
-    float2 JX = f2(j[0], j[7]), JY = f2(j[1], j[8]), JZ = f2(j[2], j[9]), JM = f2(j[3], j[10]);
-    float2 JXL = f2(j[4], j[11]), JYL = f2(j[5], j[12]), JZL = f2(j[6], j[13]);
-    float2 BX = f2(0.f, 0.f), BY = BX, BZ = BX, BP = BX;
-    auto rotate = [&]() {
-        JX = shfl2(JX, src);
-        JY = shfl2(JY, src);
-        JZ = shfl2(JZ, src);
-        JM = shfl2(JM, src);
-        if (NEAR) {
-            JXL = shfl2(JXL, src);
-            JYL = shfl2(JYL, src);
-            JZL = shfl2(JZL, src);
-        }
-        if (SYM) {
-            BX = shfl2(BX, src);
-            BY = shfl2(BY, src);
-            BZ = shfl2(BZ, src);
-            if (POT) BP = shfl2(BP, src);
-        }
-    };
-    int s0 = 0;
-    if (self_h >= 0) {
-        stepj<IRJ, NEAR, SYM, POT, true>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP, self_h);
-        rotate();
-        s0 = 1;
-    }
-#pragma unroll 2
-    for (int st = s0; st < 32; ++st) {
-        stepj<IRJ, NEAR, SYM, POT, false>(S, e2, JX, JY, JZ, JM, JXL, JYL, JZL, BX, BY, BZ, BP, -1);
-        rotate();
-    }
-    b0 = make_float4(BX.x, BY.x, BZ.x, BP.x);
-    b1 = make_float4(BX.y, BY.y, BZ.y, BP.y);
-}
-
-template <int IRJ, int MODE, bool SYM, bool POT>
-__device__ __forceinline__ void run_setj(ISetJ<IRJ> &S, const float2 e2, const float (&j)[14],
-                                         bool near, float4 &b0, float4 &b1, int self_h) {
-    if (MODE == 1 || (MODE == 2 && near))
-        rotate_setj<IRJ, true, SYM, POT>(S, e2, j, b0, b1, self_h);
-    else
-        rotate_setj<IRJ, false, SYM, POT>(S, e2, j, b0, b1, self_h);
-}
-
-__device__ __forceinline__ void load_jp(const SymParams &p, int64_t s, float (&j)[14]) {
-#pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        j[a] = __ldg(p.soa + a * p.Np + s);
-        j[7 + a] = __ldg(p.soa + a * p.Np + s + 32);
-    }
-}
-
-template <int NWJ, int IRJ, int POL, int MODE, bool POT>
-__global__ void __launch_bounds__(NWJ * 32, 1) force_symj_kernel(const SymParams p) {
-    static_assert(NWJ * 32 * IRJ == BI, "block");
-    constexpr int SNTJ = NWJ * 32;
-    constexpr int HW = IRJ / 2;  // j-sets per warp i-set
-    constexpr size_t kRedBytesJ = red_bytes_j<NWJ>();
-    extern __shared__ __align__(16) unsigned char smemj[];
-    float4 *red = reinterpret_cast<float4 *>(smemj);  // [2][KBJ][2 halves][NWJ][32]
-    Acc<POL> *tot = reinterpret_cast<Acc<POL> *>(smemj + kRedBytesJ);  // [IRJ * 4][SNTJ]
-    constexpr bool MID = POL == NB_PREC_F64ACC;
-    float *mid = reinterpret_cast<float *>(smemj + kRedBytesJ + 4 * IRJ * SNTJ * sizeof(Acc<POL>));
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-    const int64_t c = blockIdx.x;
-    int64_t u = __ldg(p.lo + c);
-    const int64_t u_end = __ldg(p.lo + c + 1);
-    if (u >= u_end) return;
-    const int F = __ldg(p.fx_exp);
-    const int64_t t0 = u / US;
-    int64_t I = 0;
-    while (row_start(I + 1, p.nb) <= t0) ++I;
-    int64_t J = I + (t0 - row_start(I, p.nb));
-    const float2 e2 = f2(p.eps2, p.eps2);
-    ISetJ<IRJ> S;
-    int half = 0;
-    bool row_open = false;
-    while (u < u_end) {
-        const int qa = (int)(u % US) * KBJ;
-        const int64_t item_end = (u / US + 1) * US;
-        const int64_t seg_end = item_end < u_end ? item_end : u_end;
-        const int qb = qa + (int)(seg_end - u) * KBJ;
-        const int64_t ib = I * BI + w * (32 * IRJ);  // this warp's i-set
-        if (!row_open) {
-#pragma unroll
-            for (int k = 0; k < IRJ; ++k) {
-                const int64_t sl = ib + 32 * k + l;
-                const float x = __ldg(p.soa + sl), y = __ldg(p.soa + p.Np + sl),
-                            z = __ldg(p.soa + 2 * p.Np + sl), m = __ldg(p.soa + 3 * p.Np + sl);
-                S.nx[k] = f2(-x, -x);
-                S.ny[k] = f2(-y, -y);
-                S.nz[k] = f2(-z, -z);
-                S.m[k] = f2(m, m);
-                S.nxl[k] = -__ldg(p.soa + 4 * p.Np + sl);
-                S.nyl[k] = -__ldg(p.soa + 5 * p.Np + sl);
-                S.nzl[k] = -__ldg(p.soa + 6 * p.Np + sl);
-                S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int v = 0; v < 4 * IRJ; ++v) {
-                tot[v * SNTJ + tid].zero();
-                if (MID) mid[v * SNTJ + tid] = 0.f;
-            }
-            row_open = true;
-        }
-        const bool sym = J != I;
-        const int64_t jb = J * BI;
-        unsigned near = 0u;
-        if (MODE == 2) {
-            float wb[7], tb[7];
-#pragma unroll
-            for (int a = 0; a < 7; ++a) {
-                wb[a] = __ldg(p.wbox + (ib / (32 * IRJ)) * 8 + a);
-                tb[a] = __ldg(p.jbox + (jb / JSJ + l) * 8 + a);
-            }
-            near = __ballot_sync(0xffffffffu, boxes_near(wb, tb, p.gamma));
-        }
-        float jn[14];
-        load_jp(p, jb + qa * JSJ + l, jn);
-        for (int q = qa; q < qb; ++q) {
-            float jc[14];
-#pragma unroll
-            for (int a = 0; a < 14; ++a) jc[a] = jn[a];
-            if (q + 1 < qb) load_jp(p, jb + (q + 1) * JSJ + l, jn);
-            const bool nq = (near >> q) & 1u;
-            float4 b0, b1;
-            if (sym) {
-                run_setj<IRJ, MODE, true, POT>(S, e2, jc, nq, b0, b1, -1);
-                float4 *r = red + (((half * KBJ + (q % KBJ)) * 2) * NWJ + w) * 32 + l;
-                r[0] = b0;
-                r[NWJ * 32] = b1;
-            } else {
-                // the warp's own slots are j-sets HW w .. HW w + HW - 1 of the block
-                run_setj<IRJ, MODE, false, POT>(S, e2, jc, nq, b0, b1,
-                                                q / HW == w ? q % HW : -1);
-            }
-            if ((q + 1) % FLJ == 0 || q + 1 == qb) {
-#pragma unroll
-                for (int k = 0; k < IRJ; ++k) {
-                    const float2 v4[4] = {S.ax[k], S.ay[k], S.az[k], S.ph[k]};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int v = (k * 4 + e) * SNTJ + tid;
-                        const float val = v4[e].x + v4[e].y;
-                        if (MID)
-                            mid[v] += val;
-                        else
-                            tot[v].add(val);
-                    }
-                    S.ax[k] = S.ay[k] = S.az[k] = S.ph[k] = f2(0.f, 0.f);
-                }
-                if (MID && ((q + 1) % FL2J == 0 || q + 1 == qb)) {
-#pragma unroll
-                    for (int v = 0; v < 4 * IRJ; ++v) {
-                        tot[v * SNTJ + tid].add(mid[v * SNTJ + tid]);
-                        mid[v * SNTJ + tid] = 0.f;
-                    }
-                }
-            }
-            if (sym && (q + 1) % KBJ == 0) {
-                __syncthreads();
-                for (int v = tid; v < KBJ * JSJ * 4; v += SNTJ) {
-                    const int e = v & 3, js = (v >> 2) & (JSJ - 1), qq = v >> 8;
-                    const float *r = reinterpret_cast<const float *>(
-                                         red + (((half * KBJ + qq) * 2 + (js >> 5)) * NWJ) * 32 +
-                                         (js & 31)) + e;
-                    float sum = 0.f;
-#pragma unroll
-                    for (int w2 = 0; w2 < NWJ; ++w2) sum += r[w2 * 32 * 4];
-                    if (POT || e < 3)
-                        add_fixed(p, e, jb + (q + 1 - KBJ + qq) * JSJ + js, e < 3 ? -sum : sum, F);
-                }
-                half ^= 1;
-            }
-        }
-        u = seg_end;
-        if ((J == p.nb - 1 && qb == NJSJ) || u == u_end) {
-#pragma unroll
-            for (int k = 0; k < IRJ; ++k) {
-                const int64_t slot = ib + 32 * k + l;
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (POT || e < 3) add_fixed(p, e, slot, tot[(k * 4 + e) * SNTJ + tid].value(), F);
-            }
-            row_open = false;
-        }
-        if (qb == NJSJ && ++J == p.nb) {
-            ++I;
-            J = I;
         }
     }
 }
@@ -912,28 +826,27 @@ __global__ void sym_ranges_kernel(const uint32_t *cost, const unsigned long long
 template <int POL, int MODE, bool POT>
 int launch_pair(const SymParams &p, cudaStream_t st) {
     auto kern = force_sym_kernel<POL, MODE, POT>;
-    const size_t smem = kRedBytes + 16 * SNT * sizeof(Acc<POL>) +
-                        (POL == NB_PREC_F64ACC ? 16 * SNT * sizeof(float) : 0);
+    const size_t smem = kRedBytes + 4 * BI * sizeof(Acc<POL>) +
+                        (POL == NB_PREC_F64ACC ? 4 * BI * sizeof(float) : 0) +
+                        (MODE == 2 ? 3 * BI * sizeof(float2) : 0);
     const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
     if (rc != NB_OK) return rc;
     kernel_timer_begin(st);
-    kern<<<(unsigned)p.ctas, SNT, smem, st>>>(p);
+    kern<<<(unsigned)p.ctas, NT, smem, st>>>(p);
     kernel_timer_end(st);
     count_launch();
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
 
-// Cost-weighted stream-K split of the items over the CTAs and the call's
-// fixed-point exponent: the kernels that run before the pair kernel.
-// JPW: warps per CTA of the j-pair kernel (0: the 32 / 128 kernel).
-template <int MODE, int JPW = 0>
+// FP64: the cost estimate per (16 warps x 32-slot j-sets), else per
+// (8 warps x 64-slot j-sets).
+template <int MODE, bool FP64 = false>
 int launch_split(const SymParams &p, const ForceJob &j, const SymLayout &y) {
-    if (JPW)
-        sym_cost_kernel<MODE, (JPW ? JPW : 1), JSJ>
-            <<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
-    else
+    if (FP64)
         sym_cost_kernel<MODE, SW, JS><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
+    else
+        sym_cost_kernel<MODE, NW, JSP><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
     sym_scan_kernel<<<1, 1024, 0, j.stream>>>(y.cost, p.T, y.prefix);
     sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
         y.cost, y.prefix, p.T, p.ctas, y.lo);
@@ -952,35 +865,8 @@ int launch_fold(const SymParams &p, const ForceJob &j, const int *perm) {
     return NB_OK;
 }
 
-template <int NWJ, int IRJ, int POL, int MODE, bool POT>
-int launch_pairj(const SymParams &p, cudaStream_t st) {
-    auto kern = force_symj_kernel<NWJ, IRJ, POL, MODE, POT>;
-    const size_t smem = red_bytes_j<NWJ>() + 4 * BI * sizeof(Acc<POL>) +
-                        (POL == NB_PREC_F64ACC ? 4 * BI * sizeof(float) : 0);
-    const int rc = smem_optin(reinterpret_cast<const void *>(kern), smem);
-    if (rc != NB_OK) return rc;
-    kernel_timer_begin(st);
-    kern<<<(unsigned)p.ctas, NWJ * 32, smem, st>>>(p);
-    kernel_timer_end(st);
-    count_launch();
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
-}
-
 template <int POL, int MODE>
 int launch_sym_mode(const SymParams &p, const ForceJob &j, const SymLayout &y, const int *perm) {
-    if (sym_jpair() == 1) {
-        NB_TRY_SYM(launch_split<MODE, 8>(p, j, y));
-        NB_TRY_SYM(j.pot ? launch_pairj<8, 8, POL, MODE, true>(p, j.stream)
-                         : launch_pairj<8, 8, POL, MODE, false>(p, j.stream));
-        return launch_fold(p, j, perm);
-    }
-    if (sym_jpair() == 2) {
-        NB_TRY_SYM(launch_split<MODE, 16>(p, j, y));
-        NB_TRY_SYM(j.pot ? launch_pairj<16, 4, POL, MODE, true>(p, j.stream)
-                         : launch_pairj<16, 4, POL, MODE, false>(p, j.stream));
-        return launch_fold(p, j, perm);
-    }
     NB_TRY_SYM(launch_split<MODE>(p, j, y));
     NB_TRY_SYM(j.pot ? launch_pair<POL, MODE, true>(p, j.stream)
                      : launch_pair<POL, MODE, false>(p, j.stream));
@@ -999,7 +885,7 @@ int launch_pair64(const SymParams64 &p, cudaStream_t st) {
 }
 
 int launch_sym64(const SymParams64 &p, const ForceJob &j, const SymLayout &y) {
-    NB_TRY_SYM(launch_split<0>(p, j, y));
+    NB_TRY_SYM(launch_split<0, true>(p, j, y));
     NB_TRY_SYM(j.pot ? launch_pair64<true>(p, j.stream) : launch_pair64<false>(p, j.stream));
     return launch_fold(p, j, nullptr);
 }
@@ -1015,14 +901,6 @@ int launch_sym_pol(const SymParams &p, const ForceJob &j, const SymLayout &y, in
 }
 
 }  // namespace
-
-int sym_jpair() {
-    static const int v = [] {
-        const char *e = getenv("NB_SYM_JPAIR");
-        return (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
-    }();
-    return v;
-}
 
 SymSizes sym_sizes(int64_t Np) {
     SymSizes z{};
