@@ -40,14 +40,15 @@
 //
 // The i-side FP32 register sums, kept per j-stream (.x, .y), are folded into
 // the accumulation policy (FP32, Kahan or FP64; totals kept in shared
-// memory) every 2 j-sets (128 terms per particle; for F64ACC through an FP32
-// middle sum in shared memory that goes into FP64 every 8 j-sets, FP64 adds
-// being slow on this part) over the CTA's segment of a row.  In Hilbert
-// order a particle's strongest, mutually cancelling terms (its spatial
-// neighbours) arrive together; with 512 terms per flush the FP32 running
-// sums of central particles of a log-normal Plummer sphere (N = 300001,
-// eps = 1e-3) lost up to 1e-5 of |a|, with 128 they stay at the 2e-6 of the
-// unsorted order.
+// memory) every 4 j-sets (128 terms per stream and particle; for F64ACC
+// through an FP32 middle sum in shared memory that goes into FP64 every 8
+// j-sets, FP64 adds being slow on this part) over the CTA's segment of a
+// row.  In Hilbert order a particle's strongest, mutually cancelling terms
+// (its spatial neighbours) arrive together; with 512-term FP32 chains the
+// running sums of central particles of a log-normal Plummer sphere
+// (N = 300001, eps = 1e-3) lost up to 1e-5 of |a|, with 128-term chains they
+// stay at the 2e-6 of the unsorted order.  (Flushing every 2 j-sets was
+// measured 0.8 % slower at 2^20 for 2.08e-6 -> 1.94e-6 worst error.)
 //
 // Combining across CTAs.  Every particle's sum collects one j-side FP32
 // partial per block above it and one i-side total per CTA that worked on its
@@ -114,7 +115,7 @@ constexpr int WS = 32 * IRP;        // i-slots per warp
 constexpr int JSP = 64;             // slots per j-set (two per lane)
 constexpr int NJSP = BI / JSP;      // j-sets per block: one 32-bit near mask
 constexpr int KBP = 2;              // j-sets per cross-warp reduction (128 slots)
-constexpr int FLP = 2;              // j-sets per i-side flush (128 terms)
+constexpr int FLP = 4;              // j-sets per i-side flush (128 terms per j-stream)
 constexpr int FL2P = 8;             // F64ACC: j-sets per flush of the FP32 middle sums
 static_assert(NW * WS == BI && NJSP == 32 && NJSP / KBP == US, "FP32 kernel shape");
 constexpr size_t kRedBytes = 2 * KBP * 2 * NW * 32 * sizeof(float4);
