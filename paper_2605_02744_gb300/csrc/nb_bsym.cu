@@ -293,13 +293,13 @@ __global__ void __launch_bounds__(256) bsym_scatter_kernel(BsParams p, int moved
     }
 }
 
-// One block per 128-slot block: optional kick (v += kick a) and drift
-// (x += dt v) of the block's particles (slot-order FP64 state), the hi/lo pack, and the
-// boxes of its four 32-slot j-sets and of the whole block (real slots only).
-__global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, double dt) {
-    const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
-    if ((int64_t)blockIdx.x * BW >= __ldg(p.totals)) return;  // whole block
-    const int i = p.perm[s];
+// The hi/lo pack of slot s (thread threadIdx.x of the block of 128 slots
+// blockIdx.x) after an optional kick (v += kick a) and drift (x += dt v) of
+// the slot-order FP64 state, and the boxes of the block's four 32-slot
+// j-sets and of the whole block (real slots only).  Called by every thread
+// of the block.
+__device__ __forceinline__ void pack_slot(const BsParams &p, int64_t s, int i, double kick,
+                                          double dt) {
     float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f}, m = 0.f;
     if (i >= 0) {
 #pragma unroll
@@ -361,6 +361,13 @@ __global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, 
         p.box128[blockIdx.x * 8 + 6] = h3[0] < l3[0] ? 0.f : amax;
         p.box128[blockIdx.x * 8 + 7] = 0.f;
     }
+}
+
+// One block per 128-slot block: pack_slot for each slot.
+__global__ void __launch_bounds__(BW) bsym_pack_kernel(BsParams p, double kick, double dt) {
+    const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
+    if ((int64_t)blockIdx.x * BW >= __ldg(p.totals)) return;  // whole block
+    pack_slot(p, s, p.perm[s], kick, dt);
 }
 
 // Persistent warps over the item queue (POT: the potential sums too).
@@ -471,6 +478,28 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
     }
 }
 
+// Slot s's total: the records of its row's items and the partials of the
+// blocks a' < a, in a fixed order and the policy's arithmetic.
+template <int POL>
+__device__ __forceinline__ void slot_sums(const BsParams &p, int64_t s, Acc<POL> (&acc4)[4]) {
+    const int64_t blk = s / BW, r = s % BW;
+    const int c = p.bsys[blk];
+    const int64_t a = blk - p.sbase[c] / BW;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc4[e].zero();
+    for (int32_t it = p.rstart[blk]; it < p.rstart[blk + 1]; ++it) {
+        const double2 *rr = reinterpret_cast<const double2 *>(p.rec + ((int64_t)it * BW + r) * 4);
+        const double2 u = __ldcs(rr), v = __ldcs(rr + 1);
+        add_record<POL>(acc4[0], u.x);
+        add_record<POL>(acc4[1], u.y);
+        add_record<POL>(acc4[2], v.x);
+        add_record<POL>(acc4[3], v.y);
+    }
+    add_partials<POL>(acc4,
+                      reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r,
+                      a, BW);
+}
+
 // Per slot: the records of its row and the partials of blocks a' < a (fixed
 // order), x G, closing kick, store; resets the queue for the next step.
 template <int POL>
@@ -481,23 +510,8 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (p.perm[s] < 0) continue;
-        const int64_t blk = s / BW, r = s % BW;
-        const int c = p.bsys[blk];
-        const int64_t a = blk - p.sbase[c] / BW;
         Acc<POL> acc4[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc4[e].zero();
-        for (int32_t it = p.rstart[blk]; it < p.rstart[blk + 1]; ++it) {
-            const double2 *rr = reinterpret_cast<const double2 *>(p.rec + ((int64_t)it * BW + r) * 4);
-            const double2 u = __ldcs(rr), v = __ldcs(rr + 1);
-            add_record<POL>(acc4[0], u.x);
-            add_record<POL>(acc4[1], u.y);
-            add_record<POL>(acc4[2], v.x);
-            add_record<POL>(acc4[3], v.y);
-        }
-        add_partials<POL>(acc4,
-                          reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r,
-                          a, BW);
+        slot_sums<POL>(p, s, acc4);
         const double ax = p.G * acc4[0].value(), ay = p.G * acc4[1].value(),
                      az = p.G * acc4[2].value();
         const double gp = -p.G * acc4[3].value();
@@ -513,6 +527,34 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
         if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
     }
     if (bad) dev::set_status(p.status, kStatusNonFinite);
+}
+
+// The fold of one step fused with the next step's opening: per slot (one
+// block per 128-slot block) the total as bsym_fold_kernel, a = G x total,
+// closing kick v += kick a, then the next step's opening kick v += kick2 a,
+// drift x += dt v and pack_slot (hi/lo pack, boxes).  The potential is not
+// stored (only the last step of a loop sums it).
+template <int POL>
+__global__ void __launch_bounds__(BW) bsym_fold_pack_kernel(BsParams p, double kick,
+                                                            double kick2, double dt) {
+    const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
+    if ((int64_t)blockIdx.x * BW >= __ldg(p.totals)) return;  // whole block
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0u;
+    const int i = p.perm[s];
+    if (i >= 0) {
+        Acc<POL> acc4[4];
+        slot_sums<POL>(p, s, acc4);
+        const double a[3] = {p.G * acc4[0].value(), p.G * acc4[1].value(),
+                             p.G * acc4[2].value()};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            st_arr(p, p.cur, 6 + d)[s] = a[d];
+            st_arr(p, p.cur, 3 + d)[s] += kick * a[d];
+        }
+        if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2])))
+            dev::set_status(p.status, kStatusNonFinite);
+    }
+    pack_slot(p, s, i, kick2, dt);
 }
 
 template <int POL, int MODE>
@@ -541,28 +583,42 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     }
     // the potential is evaluated only where the caller can see it: a
     // forces-only call, or the last step of a step loop
-    auto force = [&](double kick, bool pot) {
+    auto items = [&](bool pot) {
         if (pot)
             bsym_item_kernel<POL, MODE, true><<<item_grid, NT, item_smem, st>>>(p);
         else
             bsym_item_kernel<POL, MODE, false><<<item_grid, NT, item_smem, st>>>(p);
-        bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, kick);
-        count_launch(2);
+        count_launch();
     };
     const bool want_pot = j.pot != nullptr;
+    const double h = j.dt;
     bsym_setup_kernel<<<1, 1024, 0, st>>>(p, j.N);
     count_launch();
     sort(1);
     if (!j.acc_valid || j.nsteps == 0) {
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.0, 0.0);
-        count_launch();
-        force(0.0, want_pot && j.nsteps == 0);
+        items(want_pot && j.nsteps == 0);
+        bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, 0.0);
+        count_launch(2);
     }
+    // Step n: [re-sort] [opening kick + drift + pack] items fold.  When no
+    // re-sort separates step n from step n + 1, the fold of step n also
+    // does step n + 1's opening kick, drift and pack (one pass, one launch).
+    bool packed = false;
     for (int64_t n = 0; n < j.nsteps; ++n) {
         if (n > 0 && n % kBsResort == 0) sort(0);
-        bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.5 * j.dt, j.dt);
+        if (!packed) {
+            bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.5 * h, h);
+            count_launch();
+        }
+        const bool last = n == j.nsteps - 1;
+        items(want_pot && last);
+        packed = !last && (n + 1) % kBsResort != 0;
+        if (packed)
+            bsym_fold_pack_kernel<POL><<<pack_grid, BW, 0, st>>>(p, 0.5 * h, 0.5 * h, h);
+        else
+            bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, 0.5 * h);
         count_launch();
-        force(0.5 * j.dt, want_pot && n == j.nsteps - 1);
     }
     bsym_scatter_kernel<<<fold_grid, 256, 0, st>>>(p, j.nsteps > 0 ? 1 : 0);
     count_launch();

@@ -208,6 +208,8 @@ SymSizes sym_sizes(int64_t Np);
 // Pointers into the symmetric path's workspace regions.
 struct SymLayout {
     int *fx_exp;                   // fixed-point exponent of the call
+    unsigned long long *mmax_bits; // max |m| while it is reduced (zero between calls)
+    unsigned *arrivals;            // blocks done with the reduction (zero between calls)
     uint32_t *cost;                // per item
     unsigned long long *prefix;    // [T + 1]
     int64_t *lo;                   // [ctas + 1] stream-K range starts

@@ -524,25 +524,45 @@ __global__ void __launch_bounds__(256) sym_fold_kernel(const SymParams p, int64_
 
 // The call's fixed-point exponent from the bound N max|m| max(0.385 / eps^2,
 // 1 / eps) (x 1.02 for the rounding of FP32 partial sums) on every partial
-// and total.  One block; the maximum is exact, so F is reproducible.
-__global__ void __launch_bounds__(1024) sym_exponent_kernel(const double *__restrict__ mass,
-                                                            int64_t N, double eps,
-                                                            int *__restrict__ F) {
-    __shared__ double part[32];
+// and total.  Every block takes the maximum of its share of the masses
+// (independent loads, four per thread in flight) and folds it into one word
+// with an integer atomicMax on the bits (non-negative doubles order like
+// their bit patterns, so the maximum is exact and F reproducible); the last
+// block to finish (arrival counter) computes F and resets both words.
+__global__ void __launch_bounds__(256) sym_exponent_kernel(const double *__restrict__ mass,
+                                                           int64_t N, double eps,
+                                                           int *__restrict__ F,
+                                                           unsigned long long *mmax_bits,
+                                                           unsigned *arrivals) {
+    __shared__ double part[8];
+    __shared__ bool last;
     double m = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(mass[i]));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = i + k * stride < N ? fabs(__ldg(mass + i + k * stride)) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m = fmax(m, v[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        m = part[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) {
-            const double per = fmax(0.3849002 / (eps * eps), 1.0 / eps);
-            *F = fx::exponent_for(1.02 * (double)N * m * per);
-        }
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; ++k) m = fmax(m, part[k]);
+        atomicMax(mmax_bits, (unsigned long long)__double_as_longlong(m));
+        __threadfence();
+        last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double mm = __longlong_as_double((long long)atomicAdd(mmax_bits, 0ull));
+        const double per = fmax(0.3849002 / (eps * eps), 1.0 / eps);
+        *F = fx::exponent_for(1.02 * (double)N * mm * per);
+        *mmax_bits = 0ull;
+        *arrivals = 0u;
     }
 }
 
@@ -852,7 +872,8 @@ int launch_split(const SymParams &p, const ForceJob &j, const SymLayout &y) {
     sym_scan_kernel<<<1, 1024, 0, j.stream>>>(y.cost, p.T, y.prefix);
     sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
         y.cost, y.prefix, p.T, p.ctas, y.lo);
-    sym_exponent_kernel<<<1, 1024, 0, j.stream>>>(j.mass, j.N, j.eps, y.fx_exp);
+    sym_exponent_kernel<<<(unsigned)std::min<int64_t>(cdiv(j.N, 4 * 256), 1024), 256, 0,
+                          j.stream>>>(j.mass, j.N, j.eps, y.fx_exp, y.mmax_bits, y.arrivals);
     count_launch(4);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
@@ -921,6 +942,8 @@ SymLayout sym_layout(char *ws, const WsLayout &L) {
     SymLayout y;
     char *c = ws + L.sym_cost;
     y.fx_exp = reinterpret_cast<int *>(c);
+    y.mmax_bits = reinterpret_cast<unsigned long long *>(c + 8);
+    y.arrivals = reinterpret_cast<unsigned *>(c + 16);
     y.cost = reinterpret_cast<uint32_t *>(c + 256);
     y.prefix = reinterpret_cast<unsigned long long *>(c + 256 + align_up(4 * (size_t)z.T, 256));
     y.lo = reinterpret_cast<int64_t *>(c + 256 + align_up(4 * (size_t)z.T, 256) +

@@ -10,11 +10,11 @@ at the origin):
 * particle 1, first in order after the target, pulls it with |a| ~ 1.5, so
   the target's running total sits in [1, 2) from the first partial on;
 * the other 2^20 - 2 particles lie on a spherical cap of radius 30 around
-  +x; each pulls the target by at most 3.8e-10, so a partial sum of up to
-  128 of them stays below half a unit in the last place of the running total
+  +x; each pulls the target by at most 2.2e-10, so a partial sum of up to
+  256 of them stays below half a unit in the last place of the running total
   (5.96e-8) and is rounded away entirely by a plain FP32 add -- 2^20 of them
-  add up to ~4e-4, i.e. a relative error of ~2.6e-4 in the target's
-  acceleration (26 times the 1e-5 gate) for plain FP32 totals, while a
+  add up to ~2.1e-4, i.e. a relative error of ~1.4e-4 in the target's
+  acceleration (14 times the 1e-5 gate) for plain FP32 totals, while a
   Kahan (or an FP64) total keeps them.
 
 This is the textbook contrast between recursive summation (error growing
@@ -22,8 +22,8 @@ with the number of terms) and compensated summation (error ~2u independent
 of it), with no cancellation involved.  Displacements are split hi/lo
 (positions="split") so that rounding of the positions plays no part.  Both
 FP32-pair kernel families are checked: the direct kernel with 64-particle
-j-tiles, and the symmetric kernel, whose register sums are flushed into the
-policy every four 32-particle j-sets (128 terms).
+j-tiles, and the symmetric kernel, whose register sums (two streams of 128
+terms) are added and flushed into the policy every 256 pair terms.
 """
 import numpy as np
 import pytest
@@ -32,7 +32,7 @@ N = 1 << 20
 EPS = 0.01
 HEAVY = 1.5
 R_CAP = 30.0
-Q_MAX = 3.8e-10  # largest pull of one light particle on the target
+Q_MAX = 2.2e-10  # largest pull of one light particle on the target
 
 
 def cap_input(n=N, seed=11):
@@ -59,7 +59,7 @@ def _target_terms(pos, mass):
     return t
 
 
-@pytest.mark.parametrize("group", [64, 128])
+@pytest.mark.parametrize("group", [64, 256])
 def test_input_defeats_plain_fp32_totals_but_not_kahan(group):
     """CPU emulation of the policy step (FP32 partial sums of `group` terms
     in particle order, then an FP32 running total, plain or Kahan): the
@@ -112,5 +112,5 @@ def test_kahan_keeps_what_fp32_loses(pairs):
             assert e.max() <= 1e-5 and rel_err(p, rp).max() <= 1e-5, (pairs, prec, e.max())
     # the target: compensated totals keep the light pieces ...
     assert err["kahan"] <= 1e-6 and err["f64acc"] <= 1e-6, (pairs, err)
-    # ... which plain FP32 totals round away (expected ~2.6e-4)
+    # ... which plain FP32 totals round away (expected ~1.4e-4)
     assert err["fp32"] > 1e-4, (pairs, err)
