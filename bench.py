@@ -151,7 +151,7 @@ def _kernel_source_hash():
     a = src.index("constexpr int BI = 2048;")
     b = src.index("__global__ void __launch_bounds__(256) sym_fold_kernel(")
     h.update(src[a:b].encode())
-    for f in ("nb_sym_core.cuh", "nb_device.cuh", "nb_fixed.cuh"):
+    for f in ("nb_symj.cuh", "nb_sym_core.cuh", "nb_device.cuh", "nb_fixed.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
