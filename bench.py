@@ -667,8 +667,10 @@ def run_profile_case(args):
 
 
 def run_profile_batched(args):
-    """--profile-batched B: the batched kernel on the first B clusters of the
-    512-cluster workload, 20 KDK steps (the case its ncu capture used)."""
+    """--profile-batched B: the batched path on the first B clusters of the
+    512-cluster workload (F64ACC, dt = 1e-3): one system object, then
+    warmup + steps calls of 100 KDK steps each (the case its ncu captures
+    used)."""
     import numpy as np
     import torch
 
@@ -677,10 +679,10 @@ def run_profile_batched(args):
     pkg.build()
     sizes = ics.batched_sizes()[: args.profile_batched]
     s = ics.batched_plummer(b=len(sizes), seed=1, sizes=sizes)
+    g = api.System(s.pos, s.vel, s.mass, np.full(len(sizes), 0.01), offsets=s.offsets,
+                   precision="f64acc")
     for _ in range(args.warmup + args.steps):
-        g = api.System(s.pos, s.vel, s.mass, np.full(len(sizes), 0.01), offsets=s.offsets,
-                       precision="f64acc", tune={"cluster_ctas": 4, "threads": 256})
-        g.step(1e-3, 20)
+        g.step(1e-3, 100)
     torch.cuda.synchronize()
     return 0
 

@@ -170,6 +170,19 @@ const char *nb_version(void);
 /* Message for the last failing call on this host thread ("" if none). */
 const char *nb_last_error(void);
 
+/*
+ * Self-check of the integer-pipe float <-> double conversions and
+ * finiteness test that FP64-bound kernels use: on the host, the same
+ * source's results for every float exponent with edge significands, every
+ * double exponent with significands at the rounding boundaries, and 3 n
+ * seeded random float patterns and 2 n double patterns (splitmix64 from
+ * `seed`) are compared bit for bit with the C conversions (round to nearest
+ * even) and isfinite;
+ * *mismatches receives the count (0 when they agree).  No device work.
+ * NB_ERR_INVALID for a NULL pointer or n < 0.
+ */
+int nb_check_fp_conversions(int64_t n, uint64_t seed, int64_t *mismatches);
+
 /* Number of kernels this library has enqueued in this process (all host
  * threads).  Kernels replayed from a captured CUDA graph are not counted. */
 unsigned long long nb_launch_count(void);

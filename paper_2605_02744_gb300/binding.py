@@ -45,7 +45,8 @@ EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_workspace_bytes", "nb_forces", "nb_forces_batched", "nb_step", "nb_energy",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
             "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4",
-            "nb_kernel_timing", "nb_kernel_time", "nb_forces_range", "nb_kick_drift")
+            "nb_kernel_timing", "nb_kernel_time", "nb_forces_range", "nb_kick_drift",
+            "nb_check_fp_conversions")
 
 
 class NbError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "nb_opts_default": (None, [_OPTS]),
     "nb_version": (ctypes.c_char_p, []),
     "nb_last_error": (ctypes.c_char_p, []),
+    "nb_check_fp_conversions": (ctypes.c_int, [_i64, ctypes.c_uint64, ctypes.POINTER(_i64)]),
     "nb_launch_count": (ctypes.c_ulonglong, []),
     "nb_kernel_timing": (ctypes.c_int, [_i32]),
     "nb_kernel_time": (ctypes.c_int, [ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
@@ -188,6 +190,14 @@ def nb_version() -> str:
 
 def nb_last_error() -> str:
     return lib().nb_last_error().decode()
+
+
+def nb_check_fp_conversions(n: int, seed: int = 0) -> int:
+    """Mismatches of the integer-pipe float <-> double conversions and
+    finiteness test against the C ones (edge cases and seeded patterns)."""
+    out = _i64(0)
+    _check(lib().nb_check_fp_conversions(int(n), int(seed), ctypes.byref(out)))
+    return int(out.value)
 
 
 def nb_launch_count() -> int:

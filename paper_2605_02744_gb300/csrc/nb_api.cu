@@ -1,6 +1,8 @@
 // Host side of the C ABI (include/nbody.h): argument checks, workspace
 // layout, launch-shape choice, the leapfrog driver and CUDA-graph replay.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -13,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "nb_fpconv.cuh"
 #include "nb_internal.h"
 
 namespace nb {
@@ -398,6 +401,59 @@ const char *nb_version(void) {
 }
 
 const char *nb_last_error(void) { return g_err; }
+
+int nb_check_fp_conversions(int64_t n, uint64_t seed, int64_t *mismatches) {
+    clear_error();
+    if (!mismatches || n < 0) return fail(NB_ERR_INVALID, "need mismatches != NULL and n >= 0");
+    // splitmix64 (Steele, Lea and Flood, 2014) for the random bit patterns
+    uint64_t z = seed;
+    auto next = [&z]() {
+        uint64_t x = (z += 0x9e3779b97f4a7c15ull);
+        x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+        x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+        return x ^ (x >> 31);
+    };
+    int64_t bad = 0;
+    auto check_f = [&](uint32_t b) {
+        const float f = fpconv::from_bits_f(b);
+        const double want = (double)f, got = fpconv::f2d(f);
+        const bool same = fpconv::bits_d(got) == fpconv::bits_d(want) || (want != want && got != got);
+        if (!same) ++bad;
+    };
+    auto check_d = [&](uint64_t b) {
+        const double d = fpconv::from_bits_d(b);
+        if (fpconv::finite_d(d) != (bool)std::isfinite(d)) ++bad;
+        const float want = (float)d, got = fpconv::d2f(d);
+        if (!(fpconv::bits_f(got) == fpconv::bits_f(want) || (want != want && got != got))) ++bad;
+    };
+    // every exponent with edge significands, then random patterns
+    for (uint32_t e = 0; e < 256; ++e)
+        for (uint32_t m : {0u, 1u, 2u, 0x400000u, 0x3fffffu, 0x7fffffu, 0x123456u})
+            for (uint32_t sg : {0u, 1u}) check_f((sg << 31) | (e << 23) | m);
+    // every double exponent with significands at and around the float
+    // rounding boundaries (ties at 2^28 below the kept bits, just below,
+    // odd and even kept parts, all ones)
+    for (uint64_t e = 0; e < 2048; ++e)
+        for (uint64_t m : {0ull, 1ull, 0x10000000ull, 0x0fffffffull, 0x30000000ull, 0x20000000ull,
+                           0xffffff0000000ull, 0xfffffe0000000ull | 0x10000000ull,
+                           0xfffffffffffffull})
+            for (uint64_t sg : {0ull, 1ull}) check_d((sg << 63) | (e << 52) | m);
+    for (int64_t k = 0; k < n; ++k) {
+        const uint64_t r = next();
+        check_f((uint32_t)r);
+        check_f((uint32_t)(r >> 32));
+        check_f((uint32_t)(r >> 16) & 0x807fffffu);  // subnormals and zeros
+        check_d(r);
+        // doubles around the float range with tie and near-tie significands
+        const uint64_t e = 1023 - 160 + (r >> 56) % 300;
+        const uint64_t t = (r >> 3) & 3;
+        const uint64_t m = (r & 0xfffffe0000000ull) |
+                           (t == 0 ? 0x10000000ull : t == 1 ? 0x0fffffffull : (r & 0x1fffffffull));
+        check_d((r & 0x8000000000000000ull) | (e << 52) | m);
+    }
+    *mismatches = bad;
+    return NB_OK;
+}
 
 unsigned long long nb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "nb_device.cuh"
+#include "nb_fpconv.cuh"
 #include "nb_order.cuh"
 #include "nb_internal.h"
 #include "nb_sym_core.cuh"
@@ -20,7 +21,7 @@ using namespace symcore;
 // ================================================================ batched
 // Many independent systems (offsets [B+1], eps [B]), each unordered pair of
 // a system evaluated once as above, at warp granularity.  Every system is
-// padded to whole 128-slot blocks in Hilbert order (re-sorted every 16 steps);
+// padded to whole 128-slot blocks in Hilbert order (re-sorted every 32 steps);
 // a work item is (system c, i-block a, j-blocks [b0, b1)) with b0 >= a and at
 // most 8 j-blocks.  Persistent warps take items from an atomic queue ordered
 // largest first; a warp holds its i-block in registers (4 slots per lane),
@@ -33,7 +34,7 @@ using namespace symcore;
 constexpr int BW = 128;           // slots per warp block
 constexpr int BG = 8;             // j-blocks per item at most (default item width)
 constexpr int kBsMaxN = 8192;     // particles per system (64 blocks)
-constexpr int kBsResort = 16;     // steps between Hilbert re-sorts
+constexpr int kBsResort = 32;     // steps between Hilbert re-sorts
 // Default near/far threshold of this path (x max|x| of the two boxes): the
 // clusters are small and centred, so FP32-rounded positions stay accurate
 // closer in than in a 2^20 sphere.  512-cluster workload, 1000 steps: 2826
@@ -53,6 +54,7 @@ struct BsParams {
     int64_t *pbase;      // [B + 1] first block pair of each system
     int32_t *rstart;     // [blocks + 1] first item of each row (global block index)
     int32_t *bsys;       // [blocks] system of each block
+    int4 *bmeta;         // [blocks] first and end item of its row, first partial (block pair), a
     int4 *items;         // [items] (c, a, b0, b1)
     int32_t *order;      // [items] largest first
     unsigned *counter;   // queue head
@@ -61,9 +63,8 @@ struct BsParams {
     int64_t Ns;          // slot capacity
     int *perm;           // [Ns] slot -> particle, -1 for padding
     float *box32;        // [Ns / 32][8]
-    float *box128;       // [Ns / 128][8]
-    float *P;            // [block pairs][128][4]
-    double *rec;         // [items][128][4]
+    float *P;            // [block pairs][4][128]: planes ax ay az phi (phi only with the potential)
+    float *rec;          // [items][2][128][4]: s, then -c (KAHAN) of the i-side totals
     int64_t items_cap, pairs_cap;
     int32_t g;           // j-blocks per item at most: 2, 4 or BG
     float gamma;
@@ -84,62 +85,109 @@ __device__ __forceinline__ int64_t bs_items_of_row(int64_t nblk, int64_t a, int 
     return (nblk - a + g - 1) / g;
 }
 
+// The compensation term of a Kahan total (zero for the plain FP32 one).
+__device__ __forceinline__ float comp(const Acc<NB_PREC_KAHAN> &a) { return a.c; }
+__device__ __forceinline__ float comp(const Acc<NB_PREC_FP32> &) { return 0.f; }
+
 // Validation, padded layout, item list and its largest-first order (one
 // block of 1024 threads; the systems' sizes are fixed for the whole call).
+// Thread t owns a contiguous chunk of systems: their sizes, an exclusive
+// block-wide scan of the chunk totals (slots, items, block pairs, blocks),
+// then each system's bases, row starts and block owners.
 __global__ void __launch_bounds__(1024) bsym_setup_kernel(BsParams p, int64_t N) {
     __shared__ int64_t s_tot[4];
-    __shared__ int32_t cnt[1024][BG];
+    // the scan's [4][1024] int64 sums and the sort's [1024][BG] int32 counts
+    __shared__ __align__(16) int64_t sh[4 * 1024];
+    static_assert(sizeof(int32_t) * 1024 * BG <= sizeof(int64_t) * 4 * 1024, "count table");
+    auto cnt = reinterpret_cast<int32_t(*)[BG]>(sh);
     const int tid = threadIdx.x;
+    const int64_t chunk = (p.B + 1023) / 1024;
+    const int64_t c0 = tid * chunk < p.B ? tid * chunk : p.B;
+    const int64_t c1 = c0 + chunk < p.B ? c0 + chunk : p.B;
+    auto nblk_of = [&](int64_t c, bool report) -> int64_t {
+        const int64_t n = p.offsets[c + 1] - p.offsets[c];
+        const double e = p.eps[c];
+        if (n >= 1 && n <= kBsMaxN && e > 0.0 && isfinite(e)) return (n + BW - 1) / BW;
+        if (report) dev::set_status(p.status, kStatusInvalid);
+        return 0;
+    };
+    int64_t own[4] = {0, 0, 0, 0};  // slots, items, block pairs, blocks of the chunk
+    for (int64_t c = c0; c < c1; ++c) {
+        const int64_t nblk = nblk_of(c, true);
+        for (int64_t a = 0; a < nblk; ++a) own[1] += bs_items_of_row(nblk, a, p.g);
+        own[0] += nblk * BW;
+        own[2] += nblk * (nblk - 1) / 2;
+        own[3] += nblk;
+    }
+    // inclusive Hillis-Steele scan of the four chunk totals
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh[k * 1024 + tid] = own[k];
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = tid >= o ? sh[k * 1024 + tid - o] : 0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[k * 1024 + tid] += v[k];
+        __syncthreads();
+    }
+    int64_t base[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) base[k] = sh[k * 1024 + tid] - own[k];
     if (tid == 0) {
         if (p.offsets[0] != 0 || p.offsets[p.B] != N) dev::set_status(p.status, kStatusInvalid);
-        // prefix sums over systems (serial: once per call)
-        int64_t sb = 0, ib = 0, pb = 0, blk = 0;
-        for (int c = 0; c < p.B; ++c) {
-            const int64_t n = p.offsets[c + 1] - p.offsets[c];
-            const double e = p.eps[c];
-            int64_t nblk = 0;
-            if (n >= 1 && n <= kBsMaxN && e > 0.0 && isfinite(e))
-                nblk = (n + BW - 1) / BW;
-            else
-                dev::set_status(p.status, kStatusInvalid);
-            p.sbase[c] = sb;
-            p.ibase[c] = ib;
-            p.pbase[c] = pb;
-            int64_t it = 0;
-            for (int64_t a = 0; a < nblk; ++a) {
-                p.rstart[blk + a] = (int32_t)(ib + it);
-                p.bsys[blk + a] = c;
-                it += bs_items_of_row(nblk, a, p.g);
-            }
-            sb += nblk * BW;
-            ib += it;
-            pb += nblk * (nblk - 1) / 2;
-            blk += nblk;
-        }
-        p.sbase[p.B] = sb;
-        p.ibase[p.B] = ib;
-        p.pbase[p.B] = pb;
-        p.rstart[blk] = (int32_t)ib;
-        if (sb > p.Ns || ib > p.items_cap || pb > p.pairs_cap || p.g < 1 || p.g > BG) {
+        int64_t t[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = sh[k * 1024 + 1023];
+        if (t[0] > p.Ns || t[1] > p.items_cap || t[2] > p.pairs_cap || p.g < 1 || p.g > BG) {
             // cannot happen (bounds of bsym_layout); if it did, every system
             // becomes empty so that no kernel indexes past the buffers
             dev::set_status(p.status, kStatusInvalid);
-            sb = ib = pb = blk = 0;
-            for (int c = 0; c <= p.B; ++c) p.sbase[c] = p.ibase[c] = p.pbase[c] = 0;
+            t[0] = t[1] = t[2] = t[3] = 0;
         }
-        s_tot[0] = sb;
-        s_tot[1] = ib;
-        s_tot[2] = pb;
-        s_tot[3] = blk;
-        p.totals[0] = sb;
-        p.totals[1] = ib;
-        p.totals[2] = pb;
-        p.totals[3] = blk;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s_tot[k] = t[k];
+            p.totals[k] = t[k];
+        }
+        p.sbase[p.B] = t[0];
+        p.ibase[p.B] = t[1];
+        p.pbase[p.B] = t[2];
+        p.rstart[t[3]] = (int32_t)t[1];
         *p.counter = 0u;
+    }
+    __syncthreads();
+    if (s_tot[0] == 0) {
+        for (int64_t c = tid; c < p.B; c += blockDim.x) p.sbase[c] = p.ibase[c] = p.pbase[c] = 0;
+        return;
+    }
+    for (int64_t c = c0; c < c1; ++c) {
+        const int64_t nblk = nblk_of(c, false);
+        p.sbase[c] = base[0];
+        p.ibase[c] = base[1];
+        p.pbase[c] = base[2];
+        int64_t it = 0;
+        for (int64_t a = 0; a < nblk; ++a) {
+            p.rstart[base[3] + a] = (int32_t)(base[1] + it);
+            p.bsys[base[3] + a] = (int32_t)c;
+            it += bs_items_of_row(nblk, a, p.g);
+        }
+        base[0] += nblk * BW;
+        base[1] += it;
+        base[2] += nblk * (nblk - 1) / 2;
+        base[3] += nblk;
     }
     __syncthreads();
     const int64_t nitems = s_tot[1];
     if (s_tot[0] == 0) return;
+    // what a fold of each block reads, in one 16-byte load
+    for (int64_t b = tid; b < s_tot[3]; b += blockDim.x) {
+        const int c = p.bsys[b];
+        const int64_t a = b - p.sbase[c] / BW;
+        p.bmeta[b] = make_int4(p.rstart[b], p.rstart[b + 1], (int)(p.pbase[c] + a * (a - 1) / 2),
+                               (int)a);
+    }
     // items, one system per thread
     for (int c = tid; c < p.B; c += blockDim.x) {
         const int64_t nblk = (p.sbase[c + 1] - p.sbase[c]) / BW;
@@ -293,11 +341,36 @@ __global__ void __launch_bounds__(256) bsym_scatter_kernel(BsParams p, int moved
     }
 }
 
-// The hi/lo pack of slot s (thread threadIdx.x of the block of 128 slots
-// blockIdx.x) after an optional kick (v += kick a) and drift (x += dt v) of
-// the slot-order FP64 state, and the boxes of the block's four 32-slot
-// j-sets and of the whole block (real slots only).  Called by every thread
-// of the block.
+// The box of the 32-slot j-set of slot s (real slots only); called by the
+// 32 lanes of a warp for the 32 slots of one j-set.
+__device__ __forceinline__ void set_box(const BsParams &p, int64_t s, bool real, const float hi[3]) {
+    float bl[3], bh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bl[d] = real ? hi[d] : 3e38f;
+        bh[d] = real ? hi[d] : -3e38f;
+        for (int o = 16; o > 0; o >>= 1) {
+            bl[d] = fminf(bl[d], __shfl_xor_sync(0xffffffffu, bl[d], o));
+            bh[d] = fmaxf(bh[d], __shfl_xor_sync(0xffffffffu, bh[d], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        float amax = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            p.box32[(s / 32) * 8 + d] = bl[d];
+            p.box32[(s / 32) * 8 + 3 + d] = bh[d];
+            amax = fmaxf(amax, fmaxf(fabsf(bl[d]), fabsf(bh[d])));
+        }
+        p.box32[(s / 32) * 8 + 6] = bh[0] < bl[0] ? 0.f : amax;
+        p.box32[(s / 32) * 8 + 7] = 0.f;
+    }
+}
+
+// The hi/lo pack of slot s after an optional kick (v += kick a) and drift
+// (x += dt v) of the slot-order FP64 state, and the box of the slot's
+// 32-slot j-set (real slots only).  Called by the 32 lanes of a warp for the
+// 32 slots of one j-set.
 __device__ __forceinline__ void pack_slot(const BsParams &p, int64_t s, int i, double kick,
                                           double dt) {
     float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f}, m = 0.f;
@@ -317,50 +390,7 @@ __device__ __forceinline__ void pack_slot(const BsParams &p, int64_t s, int i, d
         m = __double2float_rn(st_arr(p, p.cur, 9)[s]);
     }
     store_packed(p.soa, p.Ns, s, hi, lo, m);
-    // boxes
-    float bl[3], bh[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        bl[d] = i >= 0 ? hi[d] : 3e38f;
-        bh[d] = i >= 0 ? hi[d] : -3e38f;
-        for (int o = 16; o > 0; o >>= 1) {
-            bl[d] = fminf(bl[d], __shfl_xor_sync(0xffffffffu, bl[d], o));
-            bh[d] = fmaxf(bh[d], __shfl_xor_sync(0xffffffffu, bh[d], o));
-        }
-    }
-    __shared__ float wb[4][6];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        float amax = 0.f;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            p.box32[(s / 32) * 8 + d] = bl[d];
-            p.box32[(s / 32) * 8 + 3 + d] = bh[d];
-            wb[w][d] = bl[d];
-            wb[w][3 + d] = bh[d];
-            amax = fmaxf(amax, fmaxf(fabsf(bl[d]), fabsf(bh[d])));
-        }
-        p.box32[(s / 32) * 8 + 6] = bh[0] < bl[0] ? 0.f : amax;
-        p.box32[(s / 32) * 8 + 7] = 0.f;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float l3[3] = {3e38f, 3e38f, 3e38f}, h3[3] = {-3e38f, -3e38f, -3e38f}, amax = 0.f;
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                l3[d] = fminf(l3[d], wb[k][d]);
-                h3[d] = fmaxf(h3[d], wb[k][3 + d]);
-            }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            p.box128[blockIdx.x * 8 + d] = l3[d];
-            p.box128[blockIdx.x * 8 + 3 + d] = h3[d];
-            amax = fmaxf(amax, fmaxf(fabsf(l3[d]), fabsf(h3[d])));
-        }
-        p.box128[blockIdx.x * 8 + 6] = h3[0] < l3[0] ? 0.f : amax;
-        p.box128[blockIdx.x * 8 + 7] = 0.f;
-    }
+    set_box(p, s, i >= 0, hi);
 }
 
 // One block per 128-slot block: pack_slot for each slot.
@@ -450,7 +480,11 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
             if (b != a) {
                 run_set2<MODE, true, POT>(S, e2, jc, nqb, bs, -1);
                 const int64_t pair = p.pbase[c] + (int64_t)b * (b - 1) / 2 + a;
-                __stcs(reinterpret_cast<float4 *>(p.P) + pair * BW + 32 * (q & 3) + l, bs);
+                float *P = p.P + pair * 4 * BW + 32 * (q & 3) + l;
+                __stcs(P, bs.x);
+                __stcs(P + BW, bs.y);
+                __stcs(P + 2 * BW, bs.z);
+                if (POT) __stcs(P + 3 * BW, bs.w);
             } else {
                 run_set2<MODE, false, POT>(S, e2, jc, nqb, bs, q & 3);
             }
@@ -469,40 +503,110 @@ __global__ void __launch_bounds__(NT, 1) bsym_item_kernel(BsParams p) {
         }
 #pragma unroll
         for (int k = 0; k < IR; ++k) {
-            double *r = p.rec + ((int64_t)idx * BW + 32 * k + l) * 4;
-            __stcs(reinterpret_cast<double2 *>(r),
-                   make_double2(tot[w][k * 4 + 0][l].value(), tot[w][k * 4 + 1][l].value()));
-            __stcs(reinterpret_cast<double2 *>(r) + 1,
-                   make_double2(tot[w][k * 4 + 2][l].value(), tot[w][k * 4 + 3][l].value()));
+            float4 *r = reinterpret_cast<float4 *>(p.rec) + (int64_t)idx * 2 * BW + 32 * k + l;
+            __stcs(r, make_float4(tot[w][k * 4 + 0][l].s, tot[w][k * 4 + 1][l].s,
+                                  tot[w][k * 4 + 2][l].s, tot[w][k * 4 + 3][l].s));
+            if (IPOL == NB_PREC_KAHAN)
+                __stcs(r + BW, make_float4(-comp(tot[w][k * 4 + 0][l]), -comp(tot[w][k * 4 + 1][l]),
+                                           -comp(tot[w][k * 4 + 2][l]), -comp(tot[w][k * 4 + 3][l])));
         }
     }
 }
 
-// Slot s's total: the records of its row's items and the partials of the
-// blocks a' < a, in a fixed order and the policy's arithmetic.
+// The F64ACC folds' accumulator: a compensated pair of floats, s + c, where
+// each add computes its exact rounding error with Knuth's TwoSum (six FP32
+// adds, valid for any magnitudes) and collects it in c.  For n adds the
+// result is within about n u^2 |sum| of the exact sum (u = 2^-24), far below
+// FP64 accumulation's own n 2^-53 for the sums of FP32 values folded here, at
+// FP32-pipe cost: FP64 adds are slow on this part and one per record or
+// group made the fold FP64-bound.
+struct TwoF {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ double value() const { return fpconv::f2d(s) + fpconv::f2d(c); }
+};
+
 template <int POL>
-__device__ __forceinline__ void slot_sums(const BsParams &p, int64_t s, Acc<POL> (&acc4)[4]) {
-    const int64_t blk = s / BW, r = s % BW;
-    const int c = p.bsys[blk];
-    const int64_t a = blk - p.sbase[c] / BW;
+struct FoldAccT {
+    using type = Acc<POL>;
+};
+template <>
+struct FoldAccT<NB_PREC_F64ACC> {
+    using type = TwoF;
+};
+template <int POL>
+using FoldAcc = typename FoldAccT<POL>::type;
+
+// Slot s's total: the records of its row's items (s, then -c for KAHAN)
+// and the partials of the blocks a' < a, in a fixed order and the policy's
+// arithmetic (F64ACC: groups of 8 partials in FP32, as the partials of
+// one tile of the direct kernel, then the compensated pair).  Loads go out
+// four records or eight partials at a time.
+template <int POL, bool POT>
+__device__ __forceinline__ void slot_sums(const BsParams &p, int64_t s, const int4 bm,
+                                          FoldAcc<POL> (&acc4)[4]) {
+    constexpr int NC = POT ? 4 : 3;  // components summed
+    const int64_t r = s % BW;
+    const int64_t a = bm.w;
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc4[e].zero();
-    for (int32_t it = p.rstart[blk]; it < p.rstart[blk + 1]; ++it) {
-        const double2 *rr = reinterpret_cast<const double2 *>(p.rec + ((int64_t)it * BW + r) * 4);
-        const double2 u = __ldcs(rr), v = __ldcs(rr + 1);
-        add_record<POL>(acc4[0], u.x);
-        add_record<POL>(acc4[1], u.y);
-        add_record<POL>(acc4[2], v.x);
-        add_record<POL>(acc4[3], v.y);
+    const int32_t r0 = bm.x, r1 = bm.y;
+    const float4 *rec = reinterpret_cast<const float4 *>(p.rec) + r;
+    for (int32_t i0 = r0; i0 < r1; i0 += 4) {
+        float4 u[4], v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t it = i0 + k < r1 ? i0 + k : r1 - 1;
+            u[k] = __ldcs(rec + it * 2 * BW);
+            if (POL == NB_PREC_KAHAN) v[k] = __ldcs(rec + it * 2 * BW + BW);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < r1) {
+                const float uu[4] = {u[k].x, u[k].y, u[k].z, u[k].w};
+                const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                for (int e = 0; e < NC; ++e) {
+                    acc4[e].add(uu[e]);
+                    if (POL == NB_PREC_KAHAN) acc4[e].add(vv[e]);
+                }
+            }
     }
-    add_partials<POL>(acc4,
-                      reinterpret_cast<const float4 *>(p.P) + (p.pbase[c] + a * (a - 1) / 2) * BW + r,
-                      a, BW);
+    const float *P = p.P + (int64_t)bm.z * 4 * BW + r;
+    for (int64_t k0 = 0; k0 < a; k0 += 8) {
+        float v[8][NC];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int e = 0; e < NC; ++e)
+                v[k][e] = k0 + k < a ? __ldcs(P + ((k0 + k) * 4 + e) * BW) : 0.f;
+#pragma unroll
+        for (int e = 0; e < NC; ++e) {
+            if (POL == NB_PREC_F64ACC) {
+                float g = v[0][e];
+#pragma unroll
+                for (int k = 1; k < 8; ++k) g += v[k][e];
+                acc4[e].add(g);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k0 + k < a) acc4[e].add(v[k][e]);
+            }
+        }
+    }
 }
 
 // Per slot: the records of its row and the partials of blocks a' < a (fixed
-// order), x G, closing kick, store; resets the queue for the next step.
-template <int POL>
+// order), x G, closing kick, store (the potential only after items that
+// summed it); resets the queue for the next step.
+template <int POL, bool POT>
 __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick) {
     const int64_t ns = __ldg(p.totals);
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0u;
@@ -510,11 +614,10 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (p.perm[s] < 0) continue;
-        Acc<POL> acc4[4];
-        slot_sums<POL>(p, s, acc4);
+        FoldAcc<POL> acc4[4];
+        slot_sums<POL, POT>(p, s, p.bmeta[s / BW], acc4);
         const double ax = p.G * acc4[0].value(), ay = p.G * acc4[1].value(),
                      az = p.G * acc4[2].value();
-        const double gp = -p.G * acc4[3].value();
         st_arr(p, p.cur, 6)[s] = ax;
         st_arr(p, p.cur, 7)[s] = ay;
         st_arr(p, p.cur, 8)[s] = az;
@@ -523,7 +626,11 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
             st_arr(p, p.cur, 4)[s] += kick * ay;
             st_arr(p, p.cur, 5)[s] += kick * az;
         }
-        p.pots[s] = gp;
+        double gp = 0.0;
+        if (POT) {
+            gp = -p.G * acc4[3].value();
+            p.pots[s] = gp;
+        }
         if (!(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(gp))) bad = 1;
     }
     if (bad) dev::set_status(p.status, kStatusNonFinite);
@@ -531,30 +638,54 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
 
 // The fold of one step fused with the next step's opening: per slot (one
 // block per 128-slot block) the total as bsym_fold_kernel, a = G x total,
-// closing kick v += kick a, then the next step's opening kick v += kick2 a,
-// drift x += dt v and pack_slot (hi/lo pack, boxes).  The potential is not
-// stored (only the last step of a loop sums it).
+// the closing kick of this step and the opening kick of the next in one
+// v += kick a (kick = h), drift x += dt v, the hi/lo pack of x and the boxes
+// (pack_slot's, without rewriting the mass plane: no re-sort came between).
+// The kernel is bound by the FP64 pipe, so its conversions between float
+// and double and its finiteness tests run on the integer pipes
+// (nb_fpconv.cuh).  Neither a nor the potential is stored: the next step's fold replaces a
+// before anything reads it, and only the last step of a loop sums the
+// potential.
 template <int POL>
-__global__ void __launch_bounds__(BW) bsym_fold_pack_kernel(BsParams p, double kick,
-                                                            double kick2, double dt) {
+__global__ void __launch_bounds__(BW) bsym_fold_pack_kernel(BsParams p, double kick, double dt) {
     const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
     if ((int64_t)blockIdx.x * BW >= __ldg(p.totals)) return;  // whole block
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0u;
     const int i = p.perm[s];
+    const int4 bm = p.bmeta[blockIdx.x];
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
     if (i >= 0) {
-        Acc<POL> acc4[4];
-        slot_sums<POL>(p, s, acc4);
-        const double a[3] = {p.G * acc4[0].value(), p.G * acc4[1].value(),
-                             p.G * acc4[2].value()};
+        // the state first: its loads overlap the sums' (the kernel is bound
+        // by the latency of its dependent loads)
+        double x0[3], v0[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            st_arr(p, p.cur, 6 + d)[s] = a[d];
-            st_arr(p, p.cur, 3 + d)[s] += kick * a[d];
+            x0[d] = st_arr(p, p.cur, d)[s];
+            v0[d] = st_arr(p, p.cur, 3 + d)[s];
         }
-        if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2])))
-            dev::set_status(p.status, kStatusNonFinite);
+        FoldAcc<POL> acc4[4];
+        slot_sums<POL, false>(p, s, bm, acc4);
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double a = acc4[d].value();
+            if (p.G != 1.0) a *= p.G;
+            ok = ok && fpconv::finite_d(a);
+            const double v = v0[d] + kick * a;
+            const double x = x0[d] + dt * v;
+            st_arr(p, p.cur, 3 + d)[s] = v;
+            st_arr(p, p.cur, d)[s] = x;
+            hi[d] = fpconv::d2f(x);
+            lo[d] = fpconv::d2f(x - fpconv::f2d(hi[d]));
+        }
+        if (!ok) dev::set_status(p.status, kStatusNonFinite);
     }
-    pack_slot(p, s, i, kick2, dt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        p.soa[d * p.Ns + s] = hi[d];
+        p.soa[(4 + d) * p.Ns + s] = lo[d];
+    }
+    set_box(p, s, i >= 0, hi);
 }
 
 template <int POL, int MODE>
@@ -598,7 +729,10 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
     if (!j.acc_valid || j.nsteps == 0) {
         bsym_pack_kernel<<<pack_grid, BW, 0, st>>>(p, 0.0, 0.0);
         items(want_pot && j.nsteps == 0);
-        bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, 0.0);
+        if (want_pot && j.nsteps == 0)
+            bsym_fold_kernel<POL, true><<<fold_grid, 256, 0, st>>>(p, 0.0);
+        else
+            bsym_fold_kernel<POL, false><<<fold_grid, 256, 0, st>>>(p, 0.0);
         count_launch(2);
     }
     // Step n: [re-sort] [opening kick + drift + pack] items fold.  When no
@@ -615,9 +749,11 @@ int launch_bsym_steps(BsParams p, const BatchedJob &j, int64_t nb_max) {
         items(want_pot && last);
         packed = !last && (n + 1) % kBsResort != 0;
         if (packed)
-            bsym_fold_pack_kernel<POL><<<pack_grid, BW, 0, st>>>(p, 0.5 * h, 0.5 * h, h);
+            bsym_fold_pack_kernel<POL><<<pack_grid, BW, 0, st>>>(p, h, h);
+        else if (want_pot && last)
+            bsym_fold_kernel<POL, true><<<fold_grid, 256, 0, st>>>(p, 0.5 * h);
         else
-            bsym_fold_kernel<POL><<<fold_grid, 256, 0, st>>>(p, 0.5 * h);
+            bsym_fold_kernel<POL, false><<<fold_grid, 256, 0, st>>>(p, 0.5 * h);
         count_launch();
     }
     bsym_scatter_kernel<<<fold_grid, 256, 0, st>>>(p, j.nsteps > 0 ? 1 : 0);
@@ -658,13 +794,13 @@ BsymLayout bsym_layout(int64_t N, int32_t B, int g) {
     z.o_pbase = take(8 * (size_t)(B + 1));
     z.o_rstart = take(4 * (size_t)(z.blocks + 1));
     z.o_bsys = take(4 * (size_t)z.blocks);
+    z.o_bmeta = take(16 * (size_t)z.blocks);
     z.o_items = take(16 * (size_t)z.items);
     z.o_order = take(4 * (size_t)z.items);
     z.o_misc = take(256);  // counter, totals
     z.o_soa = take(4 * (size_t)kPackArrays * z.Ns);
     z.o_perm = take(4 * (size_t)z.Ns);
     z.o_box32 = take(32 * (size_t)(z.Ns / 32));
-    z.o_box128 = take(32 * (size_t)z.blocks);
     z.o_P = take(16 * (size_t)BW * z.pairs);
     z.o_rec = take(32 * (size_t)BW * z.items);
     z.o_st0 = take(80 * (size_t)z.Ns);
@@ -696,6 +832,7 @@ int launch_batched_sym(const BatchedJob &j) {
     p.pbase = reinterpret_cast<int64_t *>(base + z.o_pbase);
     p.rstart = reinterpret_cast<int32_t *>(base + z.o_rstart);
     p.bsys = reinterpret_cast<int32_t *>(base + z.o_bsys);
+    p.bmeta = reinterpret_cast<int4 *>(base + z.o_bmeta);
     p.items = reinterpret_cast<int4 *>(base + z.o_items);
     p.order = reinterpret_cast<int32_t *>(base + z.o_order);
     p.counter = reinterpret_cast<unsigned *>(base + z.o_misc);
@@ -704,9 +841,8 @@ int launch_batched_sym(const BatchedJob &j) {
     p.Ns = z.Ns;
     p.perm = reinterpret_cast<int *>(base + z.o_perm);
     p.box32 = reinterpret_cast<float *>(base + z.o_box32);
-    p.box128 = reinterpret_cast<float *>(base + z.o_box128);
     p.P = reinterpret_cast<float *>(base + z.o_P);
-    p.rec = reinterpret_cast<double *>(base + z.o_rec);
+    p.rec = reinterpret_cast<float *>(base + z.o_rec);
     p.st[0] = reinterpret_cast<double *>(base + z.o_st0);
     p.st[1] = reinterpret_cast<double *>(base + z.o_st1);
     p.pots = reinterpret_cast<double *>(base + z.o_pots);

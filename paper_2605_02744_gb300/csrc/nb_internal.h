@@ -321,8 +321,8 @@ size_t batched_scratch_bytes(int32_t B);
 // asks for another width.
 struct BsymLayout {
     int64_t Ns, blocks, items, pairs;
-    size_t o_sbase, o_ibase, o_pbase, o_rstart, o_bsys, o_items, o_order, o_misc, o_soa, o_perm,
-        o_box32, o_box128, o_P, o_rec, o_st0, o_st1, o_pots, bytes;
+    size_t o_sbase, o_ibase, o_pbase, o_rstart, o_bsys, o_bmeta, o_items, o_order, o_misc, o_soa, o_perm,
+        o_box32, o_P, o_rec, o_st0, o_st1, o_pots, bytes;
 };
 BsymLayout bsym_layout(int64_t N, int32_t B, int g);
 int bsym_item_blocks(const nb_opts *opts);

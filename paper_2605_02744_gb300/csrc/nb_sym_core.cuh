@@ -1,7 +1,7 @@
 // Device pieces shared by the symmetric-pair kernels (single system:
 // nb_sym.cu; batches of systems: nb_bsym.cu): the lane-rotation evaluation
 // of one 32-particle j-set against a warp's 128 i-slots, the box test of
-// the adaptive displacement, and the policy adds of the folds.
+// the adaptive displacement.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -152,58 +152,6 @@ __device__ __forceinline__ void run_set2(ISet &S, const float2 e2, const float (
         case 1: rotate_set<1, SYM, POT>(S, e2, j, b, self_k); break;
         case 2: rotate_set<2, SYM, POT>(S, e2, j, b, self_k); break;
         default: rotate_set<3, SYM, POT>(S, e2, j, b, self_k); break;
-    }
-}
-
-// Adds an FP64 record value in the policy's arithmetic.
-template <int POL>
-__device__ __forceinline__ void add_record(Acc<POL> &a, double v);
-template <>
-__device__ __forceinline__ void add_record<NB_PREC_FP32>(Acc<NB_PREC_FP32> &a, double v) {
-    a.add((float)v);
-}
-template <>
-__device__ __forceinline__ void add_record<NB_PREC_KAHAN>(Acc<NB_PREC_KAHAN> &a, double v) {
-    const float h = (float)v;
-    a.add(h);
-    a.add((float)(v - (double)h));
-}
-template <>
-__device__ __forceinline__ void add_record<NB_PREC_F64ACC>(Acc<NB_PREC_F64ACC> &a, double v) {
-    a.s += v;
-}
-
-// Adds `count` FP32 partials (stride `stride` float4s) in order.  F64ACC adds
-// groups of 8 in FP32 first (8 x 128 or 8 x 2048 pair terms, the size of one
-// direct-kernel tile of FP32 sums) and each group's sum in FP64: FP64 adds are
-// slow on this part and one per partial made the fold FP64-bound.
-template <int POL>
-__device__ __forceinline__ void add_partials(Acc<POL> (&a)[4], const float4 *P4, int64_t count,
-                                             int64_t stride) {
-    if (POL == NB_PREC_F64ACC) {
-        for (int64_t k0 = 0; k0 < count; k0 += 8) {
-            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int64_t k1 = (k0 + 8) < count ? (k0 + 8) : count;
-            for (int64_t k = k0; k < k1; ++k) {
-                const float4 v = __ldcs(P4 + k * stride);
-                g.x += v.x;
-                g.y += v.y;
-                g.z += v.z;
-                g.w += v.w;
-            }
-            a[0].add(g.x);
-            a[1].add(g.y);
-            a[2].add(g.z);
-            a[3].add(g.w);
-        }
-    } else {
-        for (int64_t k = 0; k < count; ++k) {
-            const float4 v = __ldcs(P4 + k * stride);
-            a[0].add(v.x);
-            a[1].add(v.y);
-            a[2].add(v.z);
-            a[3].add(v.w);
-        }
     }
 }
 

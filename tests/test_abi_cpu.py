@@ -34,6 +34,16 @@ def test_every_declared_symbol_is_exported(B):
     assert sorted(B.EXPORTED) == names
 
 
+def test_integer_fp_conversions_match_c(B):
+    """The integer-pipe float <-> double conversions (round to nearest even
+    for double -> float) and finiteness test of the FP64-bound batched fold
+    give the IEEE results bit for bit."""
+    assert B.nb_check_fp_conversions(300000, seed=1) == 0
+    assert B.nb_check_fp_conversions(300000, seed=2) == 0
+    with pytest.raises(B.NbError):
+        B.nb_check_fp_conversions(-1)
+
+
 def test_version_and_defaults(B):
     assert "sm_103a" in B.nb_version()
     o = B.nb_opts()
