@@ -131,8 +131,9 @@ struct ForceJob {
 // Resolves nb_opts::positions for a precision: true = split hi/lo.
 bool positions_split(const nb_opts *opts);
 // true when the split displacement is applied only to near tile pairs of a
-// Hilbert-sorted pack (explicit NB_POS_ADAPTIVE, or the default from N >= 2^16
-// for the KAHAN and F64ACC policies; 1/64 is the default near_gamma).
+// Hilbert-sorted pack (explicit NB_POS_ADAPTIVE, or the default for the
+// KAHAN and F64ACC policies from N >= 2^18 for one evaluation and from
+// N >= 2^15 for a step loop; 1/64 is the default near_gamma).
 bool positions_adaptive(const nb_opts *opts, int64_t N, bool stepping = false);
 // Steps of one nb_step call between full re-sorts of the adaptive path.
 constexpr int64_t kResortEvery = 16;
@@ -143,7 +144,9 @@ constexpr int64_t kResortEvery = 16;
 // either box (per-pair relative displacement error <= ~sqrt(3) u / gamma,
 // u = 2^-24).  On the 2^20 Plummer and 65536 / 262144 log-normal workloads
 // the maximum relative acceleration error stayed at 1.2-2.9e-6 for every
-// gamma from 1/16 to 1/256; 1/64 keeps a factor-4 margin on the smallest.
+// gamma from 1/16 to 1/512; 1/64 is the smallest power of two whose
+// per-pair bound (6.6e-6) stays below the 1e-5 gate, so that a particle
+// whose acceleration one pair at the threshold dominates still meets it.
 constexpr float kNearFarGamma = 0.015625f;
 
 // Sub-buffers of WsLayout::sortbuf.
