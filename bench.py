@@ -344,6 +344,51 @@ def batched_rate(torch, steps=1000):
             "interactions": inter, "tune": best}
 
 
+def batched_sharded_rate(torch, ws, dev, tune, steps=1000):
+    """The 512-cluster workload split over the ranks by cluster (strong
+    scaling: the same batch on every N; clusters go largest first to the
+    least-loaded rank, and nothing is exchanged while they step): each rank
+    replays its own clusters' 1000-step CUDA graph; max over ranks of the
+    CUDA-event time; the rate counts every cluster's pairs."""
+    import numpy as np
+
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import ShardedBatch
+    s = ics.batched_plummer(512, seed=1)
+    sizes = np.diff(s.offsets).astype(np.float64)
+    eps = np.full(512, 0.01)
+    st = torch.cuda.Stream(dev)
+    with torch.cuda.stream(st):
+        g = ShardedBatch(s.pos, s.vel, s.mass, s.offsets, eps, precision="f64acc", device=dev,
+                         stream=st, use_graph=True, tune=tune)
+        if g.ops is not None:
+            sysm = g.ops.sys
+            sysm.forces()
+            sysm.step(1e-3, steps)  # first call captures the step loop as a graph
+            sysm.pos.copy_(torch.tensor(s.pos[g.rows], device=dev))
+            sysm.vel.copy_(torch.tensor(s.vel[g.rows], device=dev))
+            sysm.forces()
+        st.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(1e-3, steps)  # graph replay
+        e1.record(st)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = g.ops.poll() if g.ops is not None else 0
+    if ws > 1:
+        ms = max_over_ranks(ms, dev)
+    inter = float((sizes ** 2).sum()) * steps
+    return {"workload": f"the 512-cluster batch split over {ws} rank(s) by cluster "
+                        f"(no data exchange), {steps} KDK steps dt=1e-3 in one CUDA graph "
+                        f"per rank, F64ACC, symmetric pairs",
+            "scaling": "strong", "n_gpus": ws, "clusters_on_rank0": len(g.clusters),
+            "ms": ms, "value": inter / (ms * 1e-3) / 1e9, "unit": UNIT, "status": ok}
+
+
 def paper_workload(torch):
     """The paper's benchmark size (Sec. 4.2): 409600 particles, 3 steps of a
     Hermite scheme with acceleration + jerk (here fourth order; the paper's is
@@ -558,11 +603,18 @@ def run_ours(args):
             adj = adjoint_ratio(torch)
         except Exception as e:  # reported, never silently replaced
             adj = {"error": f"{type(e).__name__}: {e}"}
+    batched_sharded = None
     if not args.skip_extra:
         try:
             batched = batched_rate(torch)
         except Exception as e:
             batched = {"error": f"{type(e).__name__}: {e}"}
+        if ws > 1:  # on one GPU this is the batched leg itself
+            try:
+                batched_sharded = batched_sharded_rate(
+                    torch, ws, dev, batched.get("tune") if isinstance(batched, dict) else None)
+            except Exception as e:
+                batched_sharded = {"error": f"{type(e).__name__}: {e}"}
         try:
             variants = variant_rates(torch)
         except Exception as e:
@@ -636,6 +688,7 @@ def run_ours(args):
                      "lognormal_65536_per_precision": variants},
         "adjoint": adj,
         "batched": batched,
+        "batched_sharded": batched_sharded,
         "sharded": sharded,
         "paper_workload": paper,
     }

@@ -1,4 +1,6 @@
-"""One system's leapfrog split over the ranks of a process group.
+"""Work split over the ranks of a process group: one system's leapfrog by
+rows (ShardedSystem), or a batch of independent clusters by cluster
+(ShardedBatch).
 
 The particles are cut into contiguous ranges, one per rank -- the data
 decomposition of the paper's first multi-device strategy (Sec. 3.2,
@@ -26,6 +28,7 @@ from __future__ import annotations
 
 import math
 
+import numpy as np
 import torch
 
 from . import binding as B
@@ -167,4 +170,134 @@ class ShardedSystem:
                 parts = list(buf.view(self.world, self.c, 3).unbind(0))
                 dist.all_gather(parts, chunk, group=self.group)
             out.append(buf[:self.n])
+        return tuple(out)
+
+
+def partition_clusters(sizes, world: int):
+    """Cluster indices of each rank for a batch of independent systems.
+
+    Each cluster costs N_c^2 pair terms per evaluation; clusters go, largest
+    first (ties: lower index), to the rank with the least cost so far (ties:
+    lower rank).  Each rank's list is in ascending cluster order.  Clusters
+    share no particles, so nothing crosses ranks while they are stepped.
+    """
+    sizes = [int(x) for x in sizes]
+    if world < 1 or any(n < 0 for n in sizes):
+        raise ValueError("need world >= 1 and sizes >= 0")
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for c in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(c)
+        load[r] += sizes[c] ** 2
+    return [sorted(x) for x in out]
+
+
+class LibraryBatchOps:
+    """The GPU implementation for a rank's clusters: the library's batched
+    path (one api.System over them)."""
+
+    def __init__(self, pos, vel, mass, offsets, eps, precision, device, **system_kw):
+        from .api import System
+        self.sys = System(pos, vel, mass, eps, offsets=offsets, precision=precision,
+                          device=device, **system_kw)
+
+    def step(self, dt, nsteps):
+        self.sys.step(dt, nsteps)
+
+    def energy_kw(self):
+        return self.sys.energy()[:2]
+
+    def state(self):
+        return self.sys.pos, self.sys.vel, self.sys.acc
+
+    def poll(self):
+        return self.sys.poll()
+
+
+class ShardedBatch:
+    """A batch of independent clusters split over the ranks by cluster.
+
+    pos, vel, mass: all clusters' particles (array-likes [N, 3], [N, 3], [N]),
+    offsets: CSR cluster boundaries [B + 1], eps: one softening length per
+    cluster (or a scalar) -- the same on every rank.  Rank r advances the
+    clusters partition_clusters(sizes, world)[r] with the batched path; the
+    steps exchange nothing.  A cluster's arithmetic does not depend on which
+    other clusters share its launch, so each cluster's trajectory is the one
+    a single-GPU run of the whole batch gives.  world / rank default to the
+    process group's (or 1 / 0 without one); passing them runs one rank's
+    share in this process.
+    """
+
+    def __init__(self, pos, vel, mass, offsets, eps, precision="f64acc", group=None, device=None,
+                 ops=None, world=None, rank=None, **system_kw):
+        self.group = group
+        if world is None:
+            self.world, self.rank = _dist_state(group)
+            self.collective = self.world > 1
+        else:
+            self.world, self.rank = int(world), int(rank)
+            self.collective = False
+        offsets = np.asarray(offsets, dtype=np.int64)
+        sizes = np.diff(offsets)
+        b = sizes.shape[0]
+        eps_all = np.broadcast_to(np.asarray(eps, dtype=np.float64), (b,))
+        self.n = int(offsets[-1])
+        self.clusters = partition_clusters(sizes, self.world)[self.rank]
+        self.rows = (np.concatenate([np.arange(offsets[c], offsets[c + 1]) for c in self.clusters])
+                     if self.clusters else np.zeros(0, dtype=np.int64))
+        self.local_offsets = np.r_[0, np.cumsum(sizes[self.clusters])].astype(np.int64)
+        dev = torch.device(device) if device is not None else (
+            torch.device("cuda", torch.cuda.current_device()) if ops is None else
+            torch.device("cpu"))
+        self.device = dev
+        if ops is None and self.clusters:
+            pos, vel, mass = (np.asarray(a, dtype=np.float64) for a in (pos, vel, mass))
+            ops = LibraryBatchOps(pos[self.rows], vel[self.rows], mass[self.rows],
+                                  self.local_offsets, eps_all[self.clusters].copy(), precision,
+                                  dev, **system_kw)
+        elif ops is not None:
+            ops.bind(np.asarray(pos, dtype=np.float64)[self.rows],
+                     np.asarray(vel, dtype=np.float64)[self.rows],
+                     np.asarray(mass, dtype=np.float64)[self.rows], self.local_offsets,
+                     eps_all[self.clusters].copy())
+        self.ops = ops if self.clusters else None
+
+    def step(self, dt: float, nsteps: int = 1):
+        if self.ops is not None:
+            self.ops.step(dt, nsteps)
+
+    def energy(self):
+        """(K, W, E) of the whole batch (one all-reduce over the ranks)."""
+        if self.ops is not None:
+            kw = self.ops.energy_kw().clone()
+        else:
+            kw = torch.zeros(2, dtype=torch.float64, device=self.device)
+        if self.collective:
+            import torch.distributed as dist
+            dist.all_reduce(kw, group=self.group)
+        return torch.stack([kw[0], kw[1], kw[0] + kw[1]])
+
+    def local_state(self):
+        """(rows, pos, vel, acc): this rank's particle indices and state."""
+        if self.ops is None:
+            z = torch.zeros((0, 3), dtype=torch.float64, device=self.device)
+            return self.rows, z, z, z
+        return (self.rows, *self.ops.state())
+
+    def gather_state(self):
+        """Positions, velocities, accelerations of all N particles as host
+        arrays, on every rank (one all-gather of the ranks' rows)."""
+        rows, p, v, a = self.local_state()
+        mine = (rows, p.cpu().numpy(), v.cpu().numpy(), a.cpu().numpy())
+        if self.collective:
+            import torch.distributed as dist
+            parts = [None] * self.world
+            dist.all_gather_object(parts, mine, group=self.group)
+        else:
+            parts = [mine]
+        out = [np.zeros((self.n, 3)) for _ in range(3)]
+        for rows, *arrs in parts:
+            for o, x in zip(out, arrs):
+                o[rows] = x
         return tuple(out)

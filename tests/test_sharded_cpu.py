@@ -102,3 +102,108 @@ def test_sharded_leapfrog_gloo_matches_oracle(world, oracle_mod):
         assert np.abs(r[3] - xo).max() <= 1e-13 and np.abs(r[4] - vo).max() <= 1e-13
         assert np.abs(r[5] - ao).max() <= 1e-12 * np.abs(ao).max()
         assert np.allclose(r[6], [ko, wo, eo], rtol=1e-12, atol=0.0)
+
+
+# ---------------------------------------------------------------- by cluster
+def test_partition_clusters_covers_each_cluster_once_and_balances():
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import partition_clusters
+    for sizes in ([5], [3, 9, 1, 7, 7, 2], list(ics.batched_sizes())):
+        for world in (1, 2, 3, 8, 600):
+            parts = partition_clusters(sizes, world)
+            assert len(parts) == world
+            assert sorted(c for p in parts for c in p) == list(range(len(sizes)))
+            assert all(p == sorted(p) for p in parts)
+            loads = [sum(sizes[c] ** 2 for c in p) for p in parts]
+            # greedy largest-first: no rank exceeds the mean by more than one cluster
+            assert max(loads) <= sum(loads) / world + max(sizes) ** 2
+    with pytest.raises(ValueError):
+        partition_clusters([1, 2], 0)
+
+
+class OracleBatchOps:
+    """CPU stand-in for the batched path: the oracle's leapfrog per cluster
+    (test infrastructure only)."""
+
+    def bind(self, pos, vel, mass, offsets, eps):
+        self.off, self.eps, self.mass = offsets, eps, mass
+        self.pos, self.vel = pos.copy(), vel.copy()
+        self.acc = np.zeros_like(pos)
+        self.pot = np.zeros(mass.shape[0])
+        self.valid = False
+
+    def step(self, dt, nsteps):
+        import oracle
+        for c in range(len(self.eps)):
+            lo, hi = self.off[c], self.off[c + 1]
+            x, v, a, p = oracle.kdk(self.pos[lo:hi], self.vel[lo:hi], self.mass[lo:hi],
+                                    self.eps[c], dt, nsteps,
+                                    acc=self.acc[lo:hi] if self.valid else None)
+            self.pos[lo:hi], self.vel[lo:hi], self.acc[lo:hi], self.pot[lo:hi] = x, v, a, p
+        self.valid = True
+
+    def energy_kw(self):
+        k = 0.5 * (self.mass[:, None] * self.vel ** 2).sum()
+        w = 0.5 * (self.mass * self.pot).sum()
+        return torch.tensor([k, w], dtype=torch.float64)
+
+    def state(self):
+        return tuple(torch.from_numpy(a) for a in (self.pos, self.vel, self.acc))
+
+
+BATCH_SIZES = [50, 120, 33, 80, 64, 10, 90]
+
+
+def _batch_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import ShardedBatch
+    oracle.build()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        s = ics.batched_plummer(b=len(BATCH_SIZES), seed=3, sizes=BATCH_SIZES)
+        eps = np.linspace(0.01, 0.03, len(BATCH_SIZES))
+        g = ShardedBatch(s.pos, s.vel, s.mass, s.offsets, eps, ops=OracleBatchOps(), device="cpu")
+        g.step(1e-3, 3)
+        g.step(1e-3, 2)
+        pos, vel, acc = g.gather_state()
+        e = g.energy()
+        out.put((rank, g.clusters, pos, vel, acc, e.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_batch_gloo_matches_single_process(world, oracle_mod):
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import partition_clusters
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_batch_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in range(world)), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    s = ics.batched_plummer(b=len(BATCH_SIZES), seed=3, sizes=BATCH_SIZES)
+    eps = np.linspace(0.01, 0.03, len(BATCH_SIZES))
+    xo, vo, ao = np.zeros_like(s.pos), np.zeros_like(s.pos), np.zeros_like(s.pos)
+    k = w = 0.0
+    for c in range(len(BATCH_SIZES)):
+        lo, hi = s.offsets[c], s.offsets[c + 1]
+        x, v, a, p = oracle_mod.kdk(s.pos[lo:hi], s.vel[lo:hi], s.mass[lo:hi], eps[c], 1e-3, 3)
+        x, v, a, p = oracle_mod.kdk(x, v, s.mass[lo:hi], eps[c], 1e-3, 2, acc=a)
+        xo[lo:hi], vo[lo:hi], ao[lo:hi] = x, v, a
+        k += 0.5 * (s.mass[lo:hi, None] * v ** 2).sum()
+        w += 0.5 * (s.mass[lo:hi] * p).sum()
+    parts = partition_clusters(BATCH_SIZES, world)
+    for r in res:
+        assert r[1] == parts[r[0]]
+        # every rank reassembles the whole batch, equal to the single-process run
+        assert np.array_equal(r[2], xo) and np.array_equal(r[3], vo) and np.array_equal(r[4], ao)
+        assert np.allclose(r[5], [k, w, k + w], rtol=1e-13, atol=0.0)
