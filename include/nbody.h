@@ -261,8 +261,9 @@ int nb_forces_range(const double *pos, const double *mass, int64_t N, int64_t i0
  * pos, vel, acc device [n][3].  A KDK step of size h whose force evaluation
  * the caller drives itself (nb_forces_range on several GPUs) is
  * nb_kick_drift(h/2, h), the evaluation at the new positions, then
- * nb_kick_drift(h/2, 0).  NB_ERR_INVALID for n < 1, NULL or misaligned
- * arrays, non-finite kick or drift.
+ * nb_kick_drift(h/2, 0).  With drift == 0, pos is neither read nor written
+ * (it may alias vel: a plain v += kick a).  NB_ERR_INVALID for n < 1, NULL
+ * or misaligned arrays, non-finite kick or drift.
  */
 int nb_kick_drift(double *pos, double *vel, const double *acc, int64_t n, double kick,
                   double drift, const nb_opts *opts);
@@ -384,6 +385,27 @@ int nb_energy(const nb_state *s, double *out3, const nb_opts *opts);
 int nb_forces_vjp(const double *pos, const double *mass, int64_t N, double eps,
                   const double *acc_bar, const double *pot_bar, double *pos_bar,
                   double *mass_bar, void *ws, size_t ws_bytes, const nb_opts *opts);
+
+/*
+ * nb_forces_vjp for the rows i0 .. i1-1, scaled and accumulated:
+ *   pos_bar[r]  += coef * pos_bar_(i0+r),  mass_bar[r] += coef * mass_bar_(i0+r)
+ * (the sums above, each against all N).  One rank's share of a step
+ * adjoint when the particles of one system are split over several GPUs in
+ * contiguous ranges (Sec. 3.2, approach 1): the cotangents of all N
+ * (gathered each step) come in, the rank's rows go out.
+ *   pos [N][3], mass [N]            all particles (inputs)
+ *   0 <= i0 < i1 <= N               the rows
+ *   coef                            finite scale of the cotangents
+ *   acc_bar [N][3], pot_bar [N] or NULL   all particles' cotangents
+ *   pos_bar [i1-i0][3], mass_bar [i1-i0]  rows, accumulated into
+ * The workspace is sized for the whole system: nb_workspace_bytes(N, 1,
+ * opts).  Returns NB_ERR_INVALID for a bad range or non-finite coef and as
+ * nb_forces_vjp otherwise.
+ */
+int nb_forces_vjp_range(const double *pos, const double *mass, int64_t N, int64_t i0, int64_t i1,
+                        double eps, double coef, const double *acc_bar, const double *pot_bar,
+                        double *pos_bar, double *mass_bar, void *ws, size_t ws_bytes,
+                        const nb_opts *opts);
 
 /*
  * One merged reverse step of the discrete KDK adjoint at positions pos_k:

@@ -46,7 +46,7 @@ EXPORTED = ("nb_opts_default", "nb_version", "nb_last_error", "nb_tune_valid",
             "nb_forces_vjp", "nb_step_vjp", "nb_step_vjp_reverse", "nb_poll_status",
             "nb_forces_noalloc", "nb_launch_count", "nb_forces_jerk", "nb_hermite4",
             "nb_kernel_timing", "nb_kernel_time", "nb_forces_range", "nb_kick_drift",
-            "nb_check_fp_conversions")
+            "nb_check_fp_conversions", "nb_forces_vjp_range")
 
 
 class NbError(RuntimeError):
@@ -106,6 +106,8 @@ _SIGS = {
     "nb_step": (ctypes.c_int, [_STATE, _d, _i64, _OPTS]),
     "nb_energy": (ctypes.c_int, [_STATE, _vp, _OPTS]),
     "nb_forces_vjp": (ctypes.c_int, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _vp, _sz, _OPTS]),
+    "nb_forces_vjp_range": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _d, _d, _vp, _vp, _vp,
+                                           _vp, _vp, _sz, _OPTS]),
     "nb_step_vjp": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, _d, _vp, _vp, _vp, _vp, _sz, _OPTS]),
     "nb_step_vjp_reverse": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _d, _d, _d, _d, _d, _vp, _vp,
                                            _vp, _vp, _sz, _OPTS]),
@@ -301,6 +303,20 @@ def nb_forces_vjp(pos, mass, eps: float, acc_bar, pot_bar, pos_bar, mass_bar, ws
     _check(lib().nb_forces_vjp(
         _dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n, float(eps),
         _dptr(acc_bar, "acc_bar", f64), _dptr(pot_bar, "pot_bar", f64, True),
+        _dptr(pos_bar, "pos_bar", f64), _dptr(mass_bar, "mass_bar", f64), _dptr(ws, "ws"),
+        ws.numel() * ws.element_size(), ctypes.byref(opts)))
+
+
+def nb_forces_vjp_range(pos, mass, i0: int, i1: int, eps: float, coef: float, acc_bar, pot_bar,
+                        pos_bar, mass_bar, ws, opts: nb_opts):
+    """pos_bar / mass_bar (i1-i0 rows) += coef x the VJP rows i0..i1-1 of
+    the cotangents acc_bar / pot_bar of all N particles."""
+    import torch
+    f64 = torch.float64
+    n = mass.shape[0]
+    _check(lib().nb_forces_vjp_range(
+        _dptr(pos, "pos", f64), _dptr(mass, "mass", f64), n, int(i0), int(i1), float(eps),
+        float(coef), _dptr(acc_bar, "acc_bar", f64), _dptr(pot_bar, "pot_bar", f64, True),
         _dptr(pos_bar, "pos_bar", f64), _dptr(mass_bar, "mass_bar", f64), _dptr(ws, "ws"),
         ws.numel() * ws.element_size(), ctypes.byref(opts)))
 

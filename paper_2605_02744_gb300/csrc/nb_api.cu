@@ -800,6 +800,9 @@ static int make_vjp_job(VjpJob *j, const double *pos, const double *mass, int64_
     j->G = o->G;
     j->pos_bar = pos_bar;
     j->mass_bar = mass_bar;
+    j->i0 = 0;
+    j->ni = N;
+    j->kick_coef = 1.0;
     j->precision = o->precision;
     // gradients are gated at 1e-4 (median) / 1e-3 (max): single-float
     // displacements unless the caller asks for the split form
@@ -823,6 +826,29 @@ int nb_forces_vjp(const double *pos, const double *mass, int64_t N, double eps,
     j.pot_bar = pot_bar;
     j.step_form = false;
     j.accumulate = false;
+    return launch_vjp(j);
+}
+
+int nb_forces_vjp_range(const double *pos, const double *mass, int64_t N, int64_t i0, int64_t i1,
+                        double eps, double coef, const double *acc_bar, const double *pot_bar,
+                        double *pos_bar, double *mass_bar, void *ws, size_t ws_bytes,
+                        const nb_opts *o) {
+    clear_error();
+    if (i0 < 0 || i1 <= i0 || i1 > N)
+        return fail(NB_ERR_INVALID, "need 0 <= i0 < i1 <= N (got i0 = %lld, i1 = %lld, N = %lld)",
+                    (long long)i0, (long long)i1, (long long)N);
+    if (!isfinite(coef)) return fail(NB_ERR_INVALID, "coef must be finite");
+    VjpJob j;
+    NB_TRY(make_vjp_job(&j, pos, mass, N, eps, pos_bar, mass_bar, ws, ws_bytes, o));
+    NB_TRY(check_ptr(acc_bar, "acc_bar"));
+    NB_TRY(check_ptr(pot_bar, "pot_bar", true));
+    j.acc_bar = acc_bar;
+    j.pot_bar = pot_bar;
+    j.kick_coef = coef;
+    j.i0 = i0;
+    j.ni = i1 - i0;
+    j.step_form = false;
+    j.accumulate = true;
     return launch_vjp(j);
 }
 

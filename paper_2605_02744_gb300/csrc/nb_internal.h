@@ -238,9 +238,11 @@ struct VjpJob {
     double drift_dt;
     double kick_coef;
     double *vel_bar;
-    // outputs
+    // outputs: rows [i0, i0 + ni) of the N particles (pos_bar [ni][3],
+    // mass_bar [ni]); the step forms take all of them
     double *pos_bar;
     double *mass_bar;
+    int64_t i0, ni;
     bool accumulate;  // add into pos_bar/mass_bar instead of overwriting
     // optional fused force + reverse drift (nb_step_vjp_reverse)
     double *acc_out;

@@ -35,6 +35,7 @@ struct VjpParams {
     const float *csoa;  // [4][Np] cx cy cz pbar/3 (FP32)
     int64_t Np;
     int64_t N;
+    int64_t i0, ni;       // output rows [i0, i0 + ni) of the N particles
     int64_t total;
     int32_t nblocks;
     int32_t ntiles;
@@ -42,8 +43,8 @@ struct VjpParams {
     double G;
     const double *mass;   // FP64 masses (epilogue)
     const double *cdbl;   // [4][Np] FP64 cotangents c, pbar (epilogue)
-    double *pos_bar;
-    double *mass_bar;
+    double *pos_bar;      // [ni][3], row r is particle i0 + r
+    double *mass_bar;     // [ni]
     int accumulate;
     double *acc_out;      // FUSED
     double *vhalf;
@@ -58,7 +59,8 @@ struct VjpParams {
 };
 
 // -------------------------------------------------------- cotangent pack
-// Step form: vbar += drift * xbar; c = coef * vbar.  Direct form: c = abar.
+// Step form: vbar += drift * xbar; c = coef * vbar.  Direct form:
+// c = coef * abar, pbar scaled the same way.
 // Writes FP32 SoA (cx, cy, cz, pbar/3) and the FP64 copy used by the
 // epilogue and by the FP64-pair kernel.
 __global__ void pack_cotangent_kernel(const double *__restrict__ abar,
@@ -79,8 +81,8 @@ __global__ void pack_cotangent_kernel(const double *__restrict__ abar,
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 3; ++e) c[e] = abar[3 * i + e];
-                if (pbar) pb = pbar[i];
+                for (int e = 0; e < 3; ++e) c[e] = coef * abar[3 * i + e];
+                if (pbar) pb = coef * pbar[i];
             }
         }
 #pragma unroll
@@ -179,8 +181,9 @@ __device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b,
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < IR; ++k) {
-        const int64_t i = b * BI + k * NT + threadIdx.x;
-        if (i >= p.N) continue;
+        const int64_t r = b * BI + k * NT + threadIdx.x;  // output row
+        if (r >= p.ni) continue;
+        const int64_t i = p.i0 + r;
         double v[kVjpSums];
 #pragma unroll
         for (int e = 0; e < kVjpSums; ++e) v[e] = T[k][e].value();
@@ -191,15 +194,15 @@ __device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b,
         const double gz = p.G * (mk * v[2] - v[3] * cz + 3.0 * v[6]);
         const double gm = -p.G * (v[7] + (PB ? 3.0 * v[8] : 0.0));
         if (p.accumulate) {
-            p.pos_bar[3 * i] += gx;
-            p.pos_bar[3 * i + 1] += gy;
-            p.pos_bar[3 * i + 2] += gz;
-            p.mass_bar[i] += gm;
+            p.pos_bar[3 * r] += gx;
+            p.pos_bar[3 * r + 1] += gy;
+            p.pos_bar[3 * r + 2] += gz;
+            p.mass_bar[r] += gm;
         } else {
-            p.pos_bar[3 * i] = gx;
-            p.pos_bar[3 * i + 1] = gy;
-            p.pos_bar[3 * i + 2] = gz;
-            p.mass_bar[i] = gm;
+            p.pos_bar[3 * r] = gx;
+            p.pos_bar[3 * r + 1] = gy;
+            p.pos_bar[3 * r + 2] = gz;
+            p.mass_bar[r] = gm;
         }
         if (!(isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(gm))) bad = 1;
         if (FUSED) {
@@ -272,7 +275,9 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
             seg_begin = jt;
 #pragma unroll
             for (int k = 0; k < IR; ++k) {
-                const int64_t i = b * BI + k * NT + tid;
+                // rows past the range load particle i0 (their sums are never stored)
+                const int64_t r = b * BI + k * NT + tid;
+                const int64_t i = p.i0 + (r < p.ni ? r : 0);
                 const float x = p.soa[i], y = p.soa[p.Np + i], z = p.soa[2 * p.Np + i];
                 const float xl = p.soa[4 * p.Np + i], yl = p.soa[5 * p.Np + i],
                             zl = p.soa[6 * p.Np + i];
@@ -400,12 +405,14 @@ template <int NT, bool GUARD>
 __global__ void __launch_bounds__(NT)
     vjp_fp64_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
                     const double *__restrict__ cdbl, int has_pb, int64_t N, int64_t Np,
-                    double eps2, double G, double *pos_bar, double *mass_bar, int accumulate,
+                    int64_t i0, int64_t ni, double eps2, double G, double *pos_bar,
+                    double *mass_bar, int accumulate,
                     double *acc_out, double *vhalf, double *pos_rw, double rk, double rd,
                     uint32_t *status) {
     __shared__ double sx[NT], sy[NT], sz[NT], sm[NT], scx[NT], scy[NT], scz[NT], spb[NT];
-    const int64_t k = blockIdx.x * (int64_t)NT + threadIdx.x;
-    const bool live = k < N;
+    const int64_t row = blockIdx.x * (int64_t)NT + threadIdx.x;  // output row
+    const bool live = row < ni;
+    const int64_t k = i0 + (live ? row : 0);
     double xk = 0, yk = 0, zk = 0, mk = 0, cxk = 0, cyk = 0, czk = 0, pbk = 0;
     if (live) {
         xk = pos[3 * k]; yk = pos[3 * k + 1]; zk = pos[3 * k + 2]; mk = mass[k];
@@ -455,11 +462,11 @@ __global__ void __launch_bounds__(NT)
     if (!live) return;
     gx *= G; gy *= G; gz *= G; gm *= G;
     if (accumulate) {
-        pos_bar[3 * k] += gx; pos_bar[3 * k + 1] += gy; pos_bar[3 * k + 2] += gz;
-        mass_bar[k] += gm;
+        pos_bar[3 * row] += gx; pos_bar[3 * row + 1] += gy; pos_bar[3 * row + 2] += gz;
+        mass_bar[row] += gm;
     } else {
-        pos_bar[3 * k] = gx; pos_bar[3 * k + 1] = gy; pos_bar[3 * k + 2] = gz;
-        mass_bar[k] = gm;
+        pos_bar[3 * row] = gx; pos_bar[3 * row + 1] = gy; pos_bar[3 * row + 2] = gz;
+        mass_bar[row] = gm;
     }
     bool bad = !(isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(gm));
     if (acc_out) {
@@ -541,10 +548,11 @@ int launch_vjp(const VjpJob &j) {
     }
     if (j.precision == NB_PREC_FP64) {
         constexpr int NT = 128;
-        const int64_t grid = cdiv(j.N, NT);
+        const int64_t grid = cdiv(j.ni, NT);
         const double eps2 = j.eps * j.eps;
         auto k = guard ? vjp_fp64_kernel<NT, true> : vjp_fp64_kernel<NT, false>;
-        k<<<(unsigned)grid, NT, 0, j.stream>>>(j.pos, j.mass, cdbl, pb ? 1 : 0, j.N, j.L.Np, eps2,
+        k<<<(unsigned)grid, NT, 0, j.stream>>>(j.pos, j.mass, cdbl, pb ? 1 : 0, j.N, j.L.Np,
+                                               j.i0, j.ni, eps2,
                                                j.G, j.pos_bar, j.mass_bar, j.accumulate ? 1 : 0,
                                                j.acc_out, j.vhalf, j.pos_rw, j.rewind_kick,
                                                j.rewind_drift, status);
@@ -561,7 +569,9 @@ int launch_vjp(const VjpJob &j) {
     p.csoa = csoa;
     p.Np = j.L.Np;
     p.N = j.N;
-    p.nblocks = (int32_t)cdiv(j.N, sh.block_i());
+    p.i0 = j.i0;
+    p.ni = j.ni;
+    p.nblocks = (int32_t)cdiv(j.ni, sh.block_i());
     p.ntiles = (int32_t)cdiv(j.N, sh.tile_j);
     p.total = (int64_t)p.nblocks * p.ntiles;
     const float eps_f = (float)j.eps;

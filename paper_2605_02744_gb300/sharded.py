@@ -72,6 +72,16 @@ class LibraryOps:
         B.nb_energy(st, out, self.opts)
         return out[:2]
 
+    def vjp_range(self, pos_all, mass_all, eps, i0, i1, coef, abar_all, pos_bar, mass_bar):
+        """pos_bar / mass_bar (the rows) += coef x the rows' VJP of the
+        cotangents abar_all of all N particles."""
+        B.nb_forces_vjp_range(pos_all, mass_all, i0, i1, eps, coef, abar_all, None, pos_bar,
+                              mass_bar, self.ws, self.opts)
+
+    def kick(self, vel, acc, kick):
+        """vel += kick acc (the library's kick with no drift)."""
+        B.nb_kick_drift(vel, vel, acc, kick, 0.0, self.opts)
+
     def poll(self):
         return B.nb_poll_status(self.ws, self.opts)
 
@@ -127,6 +137,22 @@ class ShardedSystem:
         else:
             parts = list(self.gathered.view(self.world, self.c, 3).unbind(0))
             dist.all_gather(parts, self.chunk, group=self.group)
+
+    def gather_rows(self, rows):
+        """All N rows of a per-rank [rows, 3] tensor, in particle order (one
+        all-gather of c-row chunks)."""
+        chunk = torch.zeros((self.c, 3), dtype=rows.dtype, device=rows.device)
+        chunk[:self.rows] = rows
+        if self.world == 1:
+            return chunk[:self.n].clone()
+        out = torch.empty((self.world * self.c, 3), dtype=rows.dtype, device=rows.device)
+        import torch.distributed as dist
+        if dist.get_backend(self.group) == "nccl":
+            dist.all_gather_into_tensor(out, chunk, group=self.group)
+        else:
+            dist.all_gather(list(out.view(self.world, self.c, 3).unbind(0)), chunk,
+                            group=self.group)
+        return out[:self.n]
 
     def _forces(self):
         if self.rows > 0:
@@ -301,3 +327,49 @@ class ShardedBatch:
             for o, x in zip(out, arrs):
                 o[rows] = x
         return tuple(out)
+
+
+def sharded_loss_and_grads(pos, vel, mass, eps: float, h: float, nsteps: int, target,
+                           precision="f64acc", group=None, device=None, ops=None):
+    """L = (1/N) sum_i |x_i(T) - x*_i|^2 after nsteps KDK steps of one system
+    whose rows are split over the ranks (ShardedSystem), and the gradients of
+    L with respect to the rank's rows of the initial positions, velocities
+    and masses: the discrete adjoint of each step, unmerged.
+
+    Forward: the sharded steps, keeping the gathered positions of every step
+    ((nsteps + 1) N 24 bytes per rank).  Reverse, per step (with u the rows'
+    velocity cotangent): an all-gather of u, the rows' VJP at x_(k+1) with
+    coefficient h/2, u += h xbar, a second all-gather, the rows' VJP at x_k
+    with coefficient h/2 -- the two cotangent all-gathers of the survey's
+    multi-GPU reading.
+
+    Returns (L, xbar, vbar, mbar, (i0, i1)) with the rows' gradients.
+    """
+    g = ShardedSystem(pos, vel, mass, eps, precision=precision, group=group, device=device,
+                      ops=ops)
+    xs = [g.pos_all.clone()]
+    for _ in range(int(nsteps)):
+        g.step(h, 1)
+        xs.append(g.pos_all.clone())
+    tgt = torch.as_tensor(target, dtype=torch.float64)[g.i0:g.i1].to(g.device)
+    d = xs[-1][g.i0:g.i1] - tgt
+    part = (d * d).sum().reshape(1)
+    if g.world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(part, group=group)
+    L = float(part.item()) / g.n
+    f64 = dict(dtype=torch.float64, device=g.device)
+    xbar = (2.0 / g.n) * d
+    vbar = torch.zeros((g.rows, 3), **f64)
+    mbar = torch.zeros(g.rows, **f64)
+    for k in range(int(nsteps) - 1, -1, -1):
+        if g.rows > 0:
+            g.ops.vjp_range(xs[k + 1], g.mass, g.eps, g.i0, g.i1, 0.5 * h,
+                            g.gather_rows(vbar), xbar, mbar)
+            g.ops.kick(vbar, xbar, h)
+            g.ops.vjp_range(xs[k], g.mass, g.eps, g.i0, g.i1, 0.5 * h, g.gather_rows(vbar),
+                            xbar, mbar)
+        else:  # still take part in the collectives
+            g.gather_rows(vbar)
+            g.gather_rows(vbar)
+    return L, xbar, vbar, mbar, (g.i0, g.i1)

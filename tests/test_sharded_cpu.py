@@ -52,6 +52,16 @@ class OracleOps:
         w = 0.5 * (mass * pot).sum()
         return torch.stack([k, w])
 
+    def vjp_range(self, pos_all, mass_all, eps, i0, i1, coef, abar_all, pos_bar, mass_bar):
+        import oracle
+        xb, mb = oracle.forces_vjp(pos_all.numpy(), mass_all.numpy(), eps,
+                                   coef * abar_all.numpy())
+        pos_bar.add_(torch.from_numpy(xb[i0:i1]))
+        mass_bar.add_(torch.from_numpy(mb[i0:i1]))
+
+    def kick(self, vel, acc, kick):
+        vel.copy_(vel + kick * acc)
+
 
 def _free_port():
     with socket.socket() as s:
@@ -207,3 +217,50 @@ def test_sharded_batch_gloo_matches_single_process(world, oracle_mod):
         # every rank reassembles the whole batch, equal to the single-process run
         assert np.array_equal(r[2], xo) and np.array_equal(r[3], vo) and np.array_equal(r[4], ao)
         assert np.allclose(r[5], [k, w, k + w], rtol=1e-13, atol=0.0)
+
+
+# ------------------------------------------------------------ the adjoint
+def _adjoint_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import sharded_loss_and_grads
+    oracle.build()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        s = ics.plummer(97, seed=4)
+        target = s.pos + 0.01
+        L, xb, vb, mb, (i0, i1) = sharded_loss_and_grads(
+            s.pos, s.vel, s.mass, 0.05, 1e-3, 6, target, ops=OracleOps(), device="cpu")
+        out.put((rank, L, i0, i1, xb.numpy(), vb.numpy(), mb.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_adjoint_gloo_matches_oracle(world, oracle_mod):
+    """Two cotangent all-gathers per step and the rows' VJPs reproduce the
+    oracle's unmerged trajectory adjoint, row by row."""
+    from paper_2605_02744_gb300 import ics
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_adjoint_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in range(world)), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    s = ics.plummer(97, seed=4)
+    L, gx, gv, gm = oracle_mod.trajectory_loss_grad(s.pos, s.vel, s.mass, 0.05, 1e-3, 6,
+                                                    s.pos + 0.01)
+    for rank, Lr, i0, i1, xb, vb, mb in res:
+        assert abs(Lr - L) <= 1e-14 * abs(L)
+        scale = np.abs(np.concatenate([gx.ravel(), gv.ravel()])).max()
+        assert np.abs(xb - gx[i0:i1]).max() <= 1e-13 * scale
+        assert np.abs(vb - gv[i0:i1]).max() <= 1e-13 * scale
+        assert np.abs(mb - gm[i0:i1]).max() <= 1e-13 * np.abs(gm).max()
+    assert res[-1][3] == 97
