@@ -230,7 +230,7 @@ def _adjoint_worker(rank, world, port, out):
     oracle.build()
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        s = ics.plummer(97, seed=4)
+        s = ics.plummer(N_ADJ[world], seed=4)
         target = s.pos + 0.01
         L, xb, vb, mb, (i0, i1) = sharded_loss_and_grads(
             s.pos, s.vel, s.mass, 0.05, 1e-3, 6, target, ops=OracleOps(), device="cpu")
@@ -239,10 +239,14 @@ def _adjoint_worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+N_ADJ = {2: 97, 3: 97, 4: 5}  # 5 particles on 4 ranks: rows 2, 2, 1, 0
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_sharded_adjoint_gloo_matches_oracle(world, oracle_mod):
     """Two cotangent all-gathers per step and the rows' VJPs reproduce the
-    oracle's unmerged trajectory adjoint, row by row."""
+    oracle's unmerged trajectory adjoint, row by row (also with a rank that
+    owns no rows and only takes part in the gathers)."""
     from paper_2605_02744_gb300 import ics
     port = _free_port()
     ctx = mp.get_context("spawn")
@@ -254,13 +258,35 @@ def test_sharded_adjoint_gloo_matches_oracle(world, oracle_mod):
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    s = ics.plummer(97, seed=4)
+    n = N_ADJ[world]
+    s = ics.plummer(n, seed=4)
     L, gx, gv, gm = oracle_mod.trajectory_loss_grad(s.pos, s.vel, s.mass, 0.05, 1e-3, 6,
                                                     s.pos + 0.01)
     for rank, Lr, i0, i1, xb, vb, mb in res:
         assert abs(Lr - L) <= 1e-14 * abs(L)
+        assert xb.shape == (i1 - i0, 3) and mb.shape == (i1 - i0,)
+        if i1 == i0:
+            continue
         scale = np.abs(np.concatenate([gx.ravel(), gv.ravel()])).max()
         assert np.abs(xb - gx[i0:i1]).max() <= 1e-13 * scale
         assert np.abs(vb - gv[i0:i1]).max() <= 1e-13 * scale
         assert np.abs(mb - gm[i0:i1]).max() <= 1e-13 * np.abs(gm).max()
-    assert res[-1][3] == 97
+    assert res[-1][3] == n
+
+
+def test_sharded_batch_rank_without_clusters():
+    """More ranks than clusters: the idle rank steps nothing and reports
+    zeros."""
+    from paper_2605_02744_gb300 import ics
+    from paper_2605_02744_gb300.sharded import ShardedBatch
+    s = ics.batched_plummer(b=3, seed=3, sizes=[20, 30, 40])
+    g = ShardedBatch(s.pos, s.vel, s.mass, s.offsets, 0.02, ops=OracleBatchOps(), world=5,
+                     rank=4, device="cpu")
+    assert g.clusters == [] and g.ops is None and g.rows.size == 0
+    g.step(1e-3, 3)
+    assert g.energy().tolist() == [0.0, 0.0, 0.0]
+    rows, p, v, a = g.local_state()
+    assert rows.size == 0 and p.shape == (0, 3)
+    busy = ShardedBatch(s.pos, s.vel, s.mass, s.offsets, 0.02, ops=OracleBatchOps(), world=5,
+                        rank=0, device="cpu")
+    assert busy.clusters == [2]
