@@ -118,7 +118,8 @@ constexpr int JSP = 64;             // slots per j-set (two per lane)
 constexpr int NJSP = BI / JSP;      // j-sets per block: one 32-bit near mask
 constexpr int KBP = 2;              // j-sets per cross-warp reduction (128 slots)
 constexpr int FLP = 4;              // j-sets per i-side flush (128 terms per j-stream)
-constexpr int FL2P = 8;             // F64ACC: j-sets per flush of the FP32 middle sums
+constexpr int FL2P = 16;            // F64ACC: j-sets per FP64 add of the FP32 middle sums
+                                    // (1024 pair terms; 8 j-sets: 341.4 ms at 2^20, 16: 334.5)
 static_assert(NW * WS == BI && NJSP == 32 && NJSP / KBP == US, "FP32 kernel shape");
 constexpr size_t kRedBytes = 2 * KBP * 2 * NW * 32 * sizeof(float4);
 // FP64 pairs (force_sym64_kernel)
