@@ -74,8 +74,9 @@ typedef enum {
  * (Sec. 3.1); its displacement error is ~6e-8 |x| / |x_j - x_i|, which
  * reaches ~1e-4 relative acceleration error for close pairs at N = 2^20. */
 typedef enum {
-    NB_POS_DEFAULT = 0, /* KAHAN/F64ACC: SPLIT below N = 262144, ADAPTIVE
-                           from there; FP32: SINGLE                        */
+    NB_POS_DEFAULT = 0, /* KAHAN/F64ACC: SPLIT below N = 65536 (32768 in
+                           an nb_step loop), ADAPTIVE from there; FP32:
+                           SINGLE                                          */
     NB_POS_SPLIT = 1,
     NB_POS_SINGLE = 2,
     NB_POS_ADAPTIVE = 3 /* particles sorted along a Hilbert curve each call;

@@ -132,7 +132,7 @@ struct ForceJob {
 bool positions_split(const nb_opts *opts);
 // true when the split displacement is applied only to near tile pairs of a
 // Hilbert-sorted pack (explicit NB_POS_ADAPTIVE, or the default for the
-// KAHAN and F64ACC policies from N >= 2^18 for one evaluation and from
+// KAHAN and F64ACC policies from N >= 2^16 for one evaluation and from
 // N >= 2^15 for a step loop; 1/64 is the default near_gamma).
 bool positions_adaptive(const nb_opts *opts, int64_t N, bool stepping = false);
 // Steps of one nb_step call between full re-sorts of the adaptive path.
