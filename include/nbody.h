@@ -101,7 +101,7 @@ typedef enum {
  * N max|m| max(0.385 / eps^2, 1 / eps) on every acceleration component and
  * potential; it is finer than FP64 rounding unless that bound exceeds the
  * smallest |a_i| by more than ~10^14.  DEFAULT takes SYMMETRIC for
- * 32768 <= N <= 2^24 and eps > 0 (FP32 and FP64 pairs), DIRECT otherwise.
+ * 24576 <= N <= 2^24 and eps > 0 (FP32 and FP64 pairs), DIRECT otherwise.
  * For batches (B > 1, nb_forces_batched and
  * nb_step with offsets) DEFAULT and SYMMETRIC take the symmetric batched
  * path (warp-granular work items; workspace about 250 B per particle plus

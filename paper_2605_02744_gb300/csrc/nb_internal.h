@@ -199,9 +199,12 @@ int launch_force(const ForceJob &job);
 // Row blocks of 2048 slots; items are the block pairs (I, J >= I).
 constexpr int64_t kSymBlock = 2048;
 // Default size range of the symmetric-pair path (its scratch is O(N): 64 B
-// per particle of fixed-point totals plus 12 B per block pair of cost
-// estimates, 25 MB at N = 2^22, 400 MB at 2^24).
-constexpr int64_t kSymMinN = 1 << 15;
+// per particle of fixed-point totals, 268 MB at N = 2^22, plus 12 B per
+// block pair of cost estimates, 25 MB at 2^22, 400 MB at 2^24).  Below the
+// lower end the direct kernel is faster (Kahan evaluation, direct /
+// symmetric: 0.185 / 0.232 ms at 16384, 0.386 / 0.365 at 24576, 0.673 /
+// 0.552 at 32768).
+constexpr int64_t kSymMinN = 24576;
 constexpr int64_t kSymMaxN = 1 << 24;
 struct SymSizes {
     int64_t nb, T, U, ctas;  // row blocks, items, stream-K units, CTAs
