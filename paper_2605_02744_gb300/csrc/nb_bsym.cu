@@ -643,9 +643,9 @@ __global__ void __launch_bounds__(256) bsym_fold_kernel(BsParams p, double kick)
 // (pack_slot's, without rewriting the mass plane: no re-sort came between).
 // The kernel is bound by the FP64 pipe, so its conversions between float
 // and double and its finiteness tests run on the integer pipes
-// (nb_fpconv.cuh).  Neither a nor the potential is stored: the next step's fold replaces a
-// before anything reads it, and only the last step of a loop sums the
-// potential.
+// (nb_fpconv.cuh).  Neither a nor the potential is stored: the next step's
+// fold replaces a before anything reads it, and only the last step of a
+// loop sums the potential.
 template <int POL>
 __global__ void __launch_bounds__(BW) bsym_fold_pack_kernel(BsParams p, double kick, double dt) {
     const int64_t s = (int64_t)blockIdx.x * BW + threadIdx.x;
