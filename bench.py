@@ -719,6 +719,23 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_adjoint(args):
+    """--profile-adjoint: the adjoint workload once (16384 particles, 200
+    KDK steps of 1e-3, eps 5e-3, F64ACC): the forward steps and one
+    time-reversed gradient (the case its ncu captures used)."""
+    import torch
+
+    import paper_2605_02744_gb300 as pkg
+    from paper_2605_02744_gb300 import adjoint, ics
+    pkg.build()
+    s = ics.plummer(16384, seed=0)
+    target = ics.perturb_positions(s.pos, 1e-3, seed=2)
+    adjoint.time_forward_backward(s, target, eps=5e-3, dt=1e-3, nsteps=200, segment=20,
+                                  precision="f64acc", modes=("reverse",), reps=1)
+    torch.cuda.synchronize()
+    return 0
+
+
 def run_profile_batched(args):
     """--profile-batched B: the batched path on the first B clusters of the
     512-cluster workload (F64ACC, dt = 1e-3): one system object, then
@@ -756,6 +773,8 @@ def main():
     ap.add_argument("--precision", default="kahan")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="run only the batched kernel on this many clusters (for ncu)")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="run only the adjoint workload's forward and one gradient (for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
@@ -764,6 +783,8 @@ def main():
         return run_profile_case(args)
     if args.profile_batched:
         return run_profile_batched(args)
+    if args.profile_adjoint:
+        return run_profile_adjoint(args)
     return run_ours(args)
 
 

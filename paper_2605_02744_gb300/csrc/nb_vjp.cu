@@ -174,9 +174,16 @@ __device__ __forceinline__ constexpr bool vjp_sum_live(int e) {
     return e < 8 || (e == 8 && PB) || (e >= 9 && FUSED);
 }
 
+// The FP64 totals of a thread's output rows live in shared memory,
+// [kVjpSums][IR][NT] (added to once per j-tile; in registers they took 52
+// of the thread's registers and held the kernel at 2 CTAs per SM).
+template <int NT, int IR>
+__device__ __forceinline__ double &tot_at(double *T, int k, int e) {
+    return T[(e * IR + k) * NT + threadIdx.x];
+}
+
 template <int NT, int IR, bool PB, bool FUSED>
-__device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b,
-                                             const Acc<NB_PREC_F64ACC> (&T)[IR][kVjpSums]) {
+__device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b, double *T) {
     constexpr int BI = NT * IR;
     uint32_t bad = 0;
 #pragma unroll
@@ -186,7 +193,7 @@ __device__ __forceinline__ void vjp_epilogue(const VjpParams &p, int64_t b,
         const int64_t i = p.i0 + r;
         double v[kVjpSums];
 #pragma unroll
-        for (int e = 0; e < kVjpSums; ++e) v[e] = T[k][e].value();
+        for (int e = 0; e < kVjpSums; ++e) v[e] = vjp_sum_live<PB, FUSED>(e) ? tot_at<NT, IR>(T, k, e) : 0.0;
         const double mk = p.mass[i];
         const double cx = p.cdbl[i], cy = p.cdbl[p.Np + i], cz = p.cdbl[2 * p.Np + i];
         const double gx = p.G * (mk * v[0] - v[3] * cx + 3.0 * v[4]);
@@ -228,6 +235,7 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + ST * NC * 4 * TJ);
+    double *T = reinterpret_cast<double *>(smem_raw + ST * NC * 4 * TJ + ST * 8);
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
@@ -262,7 +270,6 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
     float2 nx[IR], ny[IR], nz[IR], nxl[IR], nyl[IR], nzl[IR], nmk[IR], cxk[IR], cyk[IR],
         czk[IR], npbk[IR];
     int kidx[IR];
-    Acc<NB_PREC_F64ACC> T[IR][kVjpSums];
     const float2 eps2 = f2(p.eps2, p.eps2);
     int64_t b = 0, seg_begin = 0;
     const int64_t first_block = L0 / p.ntiles;
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
                 czk[k] = f2(cz, cz);
                 npbk[k] = f2(-pb, -pb);
 #pragma unroll
-                for (int e = 0; e < kVjpSums; ++e) T[k][e].zero();
+                for (int e = 0; e < kVjpSums; ++e) tot_at<NT, IR>(T, k, e) = 0.0;
             }
         }
         const int s = (int)(q % ST);
@@ -333,7 +340,8 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
         for (int k = 0; k < IR; ++k)
 #pragma unroll
             for (int e = 0; e < kVjpSums; ++e)
-                if (vjp_sum_live<PB, FUSED>(e)) T[k][e].add(S[k][e].x + S[k][e].y);
+                if (vjp_sum_live<PB, FUSED>(e))
+                    tot_at<NT, IR>(T, k, e) += (double)(S[k][e].x + S[k][e].y);
 
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -364,7 +372,8 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
                 for (int k = 0; k < IR; ++k)
 #pragma unroll
                     for (int e = 0; e < kVjpSums; ++e)
-                        if (vjp_sum_live<PB, FUSED>(e)) rec[(k * NT + tid) * 16 + e] = T[k][e].s;
+                        if (vjp_sum_live<PB, FUSED>(e))
+                            rec[(k * NT + tid) * 16 + e] = tot_at<NT, IR>(T, k, e);
                 __threadfence();
                 __syncthreads();
                 const int64_t cf = sk_owner(p.total, C, b * p.ntiles);
@@ -379,7 +388,7 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
 #pragma unroll
                     for (int k = 0; k < IR; ++k)
 #pragma unroll
-                        for (int e = 0; e < kVjpSums; ++e) T[k][e].zero();
+                        for (int e = 0; e < kVjpSums; ++e) tot_at<NT, IR>(T, k, e) = 0.0;
                     for (int64_t cc = cf; cc <= cl; ++cc) {
                         const int sl = (b == sk_lo(p.total, C, cc) / p.ntiles) ? 0 : 1;
                         const double *r = p.records + ((2 * cc + sl) * BI) * 16;
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(NT) vjp_sk_kernel(const VjpParams p) {
 #pragma unroll
                             for (int e = 0; e < kVjpSums; ++e)
                                 if (vjp_sum_live<PB, FUSED>(e))
-                                    T[k][e].s += __ldcg(r + (k * NT + tid) * 16 + e);
+                                    tot_at<NT, IR>(T, k, e) += __ldcg(r + (k * NT + tid) * 16 + e);
                     }
                     vjp_epilogue<NT, IR, PB, FUSED>(p, b, T);
                     if (tid == 0) p.counters[b] = 0u;
@@ -500,7 +509,8 @@ bool vjp_shape_compiled(const Shape &s) {
 template <int NT, int IR, int TJ, int ST, bool GUARD, bool PB, bool FUSED, bool SPLIT>
 static int launch_vjp_sk(const VjpParams &p, int cps, cudaStream_t st) {
     auto kern = vjp_sk_kernel<NT, IR, TJ, ST, GUARD, PB, FUSED, SPLIT>;
-    const size_t smem = (size_t)ST * 11 * 4 * TJ + (size_t)ST * 8;
+    const size_t smem = (size_t)ST * 11 * 4 * TJ + (size_t)ST * 8 +
+                        (size_t)kVjpSums * IR * NT * sizeof(double);
     static const int occ = occupancy(reinterpret_cast<const void *>(kern), NT, smem);
     const int grid = persistent_grid(cps, occ, p.total);
     kern<<<grid, NT, smem, st>>>(p);
