@@ -274,3 +274,24 @@ def test_symmetric_batched_refuses_other_item_widths():
                                   None, ws, opts)
     assert e.value.code == binding.NB_ERR_INVALID
     assert np.all(host(acc) == 0.0)
+
+
+@pytest.mark.parametrize("prec,tol", [("kahan", 1e-5), ("fp32", 1e-4)])
+def test_symmetric_batched_step_loop_with_G(prec, tol):
+    """The fused fold-and-pack of the step loop (merged kicks, G applied
+    only when G != 1) under the Kahan and FP32 policies, across a re-sort,
+    against the oracle's leapfrog of every cluster with the same G."""
+    sizes = [700, 64, 2100, 129]
+    s = _batch(sizes, seed=8)
+    eps = _eps(len(sizes), 8)
+    G, h, steps = 0.75, 1e-3, 40
+    g = api.System(s.pos, s.vel, s.mass, eps, offsets=s.offsets, precision=prec, G=G)
+    g.step(h, steps)
+    assert g.poll() == binding.NB_OK
+    x, v, a = host(g.pos), host(g.vel), host(g.acc)
+    for c in range(len(sizes)):
+        lo, hi = s.offsets[c], s.offsets[c + 1]
+        xo, vo, ao, _ = oracle.kdk(s.pos[lo:hi], s.vel[lo:hi], s.mass[lo:hi], eps[c], h, steps, G)
+        assert rel_vec_err(a[lo:hi], ao).max() <= tol, (prec, c)
+        assert np.abs(x[lo:hi] - xo).max() <= 50 * tol * h * h * steps * np.abs(ao).max(), (prec, c)
+        assert np.abs(v[lo:hi] - vo).max() <= 10 * tol * h * steps * np.abs(ao).max(), (prec, c)
