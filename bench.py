@@ -174,12 +174,14 @@ def _traffic():
     return float(vals["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in vals else None
 
 
-def cpu_baseline(seconds: float = 10.0, gpu=None):
+def cpu_baseline(seconds: float = 10.0, gpu=None, gpu65536=None):
     """FP64 oracle rows on the host cores: exact a_i, phi_i for sampled i.
 
     `gpu`: {name: (acc [N, 3], pot [N])} from GPU evaluations at the same
     positions; their errors on the sampled rows are returned as a second
-    value (see accuracy_on_rows)."""
+    value (see accuracy_on_rows).  `gpu65536`: the same for the 65536
+    log-normal workload's precision variants, compared with the rows the
+    oracle computes for its rate on that workload."""
     import numpy as np
 
     import oracle
@@ -200,24 +202,35 @@ def cpu_baseline(seconds: float = 10.0, gpu=None):
     info = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{nrows} exact rows x {N_MAIN} j of the 2^20 Plummer sphere "
                       f"(FP64 C, OpenMP over rows), {el:.1f} s",
-            "other_sizes": _oracle_other_sizes()}
+            }
+    info["other_sizes"], exact = _oracle_other_sizes()
     acc = None
     if gpu:
         acc = {"rows": nrows, "reference": "the FP64 oracle's exact rows above",
                "gate": 1e-5}
         for name, (a, p) in gpu.items():
             acc[name] = accuracy_on_rows(a[rows], p[rows], ra, rp)
+    if gpu65536 and acc is not None:
+        r65, ra65, rp65 = exact["plummer_lognormal_65536"]
+        acc["lognormal_65536"] = {
+            "rows": int(r65.shape[0]),
+            "reference": "the oracle's exact rows of other_sizes.plummer_lognormal_65536",
+            "gates_in_tests": {"f64acc": 1e-5, "kahan": 1e-5, "fp64": 1e-12,
+                               "fp32": "none (single-float displacements)"},
+            **{name: accuracy_on_rows(a[r65], p[r65], ra65, rp65)
+               for name, (a, p) in gpu65536.items()}}
     return info, acc
 
 
 def _oracle_other_sizes(seconds: float = 2.0):
     """The oracle's rate on the 65536 log-normal and 16384 Plummer workloads
-    (sampled rows against all j, about `seconds` each), for comparison."""
+    (sampled rows against all j, about `seconds` each), for comparison, and
+    those exact rows ({name: (rows, acc, pot)})."""
     import numpy as np
 
     import oracle
     from paper_2605_02744_gb300 import ics
-    out = {}
+    out, exact = {}, {}
     for name, s, eps in (("plummer_lognormal_65536", ics.plummer_lognormal(65536, 0), 1e-3),
                          ("plummer_16384", ics.plummer(16384, 0), 5e-3)):
         n = s.mass.shape[0]
@@ -228,10 +241,11 @@ def _oracle_other_sizes(seconds: float = 2.0):
         nrows = int(max(256, min(n, 256 * seconds / max(dt, 1e-3))))
         rows = rng.choice(n, nrows, replace=False)
         t0 = time.perf_counter()
-        oracle.forces_rows(s.pos, s.mass, eps, rows)
+        ra, rp = oracle.forces_rows(s.pos, s.mass, eps, rows)
         el = time.perf_counter() - t0
         out[name] = {"value": nrows * n / el / 1e9, "unit": UNIT, "rows": nrows}
-    return out
+        exact[name] = (rows, ra, rp)
+    return out, exact
 
 
 def accuracy_on_rows(a, p, ra, rp):
@@ -427,13 +441,18 @@ def paper_workload(torch):
 
 def variant_rates(torch):
     """The 65536-particle log-normal workload: 10 KDK steps dt=1e-4 per
-    precision variant (nb_step loop, energy not included)."""
+    precision variant (nb_step loop, energy not included).  Also returns
+    each variant's forces at the initial positions (untimed), which the
+    oracle leg compares with its exact rows."""
     from paper_2605_02744_gb300 import api, ics
     s = ics.plummer_lognormal(65536, seed=0)
     out = {"workload": "Plummer N=65536, log-normal masses (sigma 0.5), eps=1e-3, "
                        "10 KDK steps dt=1e-4"}
+    first = {}
     for prec in ("f64acc", "kahan", "fp32", "fp64"):
         g = api.System(s.pos, s.vel, s.mass, 1e-3, precision=prec)
+        g.forces()
+        first[prec] = (g.acc.cpu().numpy(), g.pot.cpu().numpy())
         g.step(1e-4, 1)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -444,7 +463,7 @@ def variant_rates(torch):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         out[prec] = {"ms_10_steps": ms, "value": 10 * 65536.0 ** 2 / (ms * 1e-3) / 1e9}
-    return out
+    return out, first
 
 
 def adjoint_ratio(torch):
@@ -592,7 +611,7 @@ def run_ours(args):
     d2h = sum(v.numel() * 8 for v in outs.values()) + 24
     del e2e_sys
 
-    adj = batched = variants = paper = sharded = None
+    adj = batched = variants = paper = sharded = first65536 = None
     if not args.skip_extra:
         try:
             sharded = sharded_rate(torch, args, ws, dev)
@@ -616,7 +635,7 @@ def run_ours(args):
             except Exception as e:
                 batched_sharded = {"error": f"{type(e).__name__}: {e}"}
         try:
-            variants = variant_rates(torch)
+            variants, first65536 = variant_rates(torch)
         except Exception as e:
             variants = {"error": f"{type(e).__name__}: {e}"}
         try:
@@ -693,7 +712,8 @@ def run_ours(args):
         "paper_workload": paper,
     }
     if ws == 1 and not args.skip_cpu:
-        line["cpu_baseline"], line["accuracy"] = cpu_baseline(args.cpu_seconds, first)
+        line["cpu_baseline"], line["accuracy"] = cpu_baseline(args.cpu_seconds, first,
+                                                              first65536)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
