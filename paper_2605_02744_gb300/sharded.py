@@ -340,8 +340,8 @@ def sharded_loss_and_grads(pos, vel, mass, eps: float, h: float, nsteps: int, ta
     ((nsteps + 1) N 24 bytes per rank).  Reverse, per step (with u the rows'
     velocity cotangent): an all-gather of u, the rows' VJP at x_(k+1) with
     coefficient h/2, u += h xbar, a second all-gather, the rows' VJP at x_k
-    with coefficient h/2 -- the two cotangent all-gathers of the survey's
-    multi-GPU reading.
+    with coefficient h/2: two all-gathers of cotangents per step on top of
+    the forward pass's one of positions.
 
     Returns (L, xbar, vbar, mbar, (i0, i1)) with the rows' gradients.
     """
