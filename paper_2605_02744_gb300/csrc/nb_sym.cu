@@ -587,13 +587,17 @@ __global__ void __launch_bounds__(SNT, CPS) force_sym64_kernel(const SymParams64
 }
 
 // ------------------------------------------------ cost-weighted stream-K
-// Relative cost of one (warp, j-set) of an item.  Far pairs: the FP32 pipe
-// cycles per lane and step (off-diagonal 18, diagonal i-side only 13).  Near
-// pairs take 24 / 19 pipe cycles, but a near j-set of one warp also holds
-// its 15 siblings at the next barrier; weighted 36 / 28 the per-CTA timers
-// of a 2^20 Plummer evaluation end within 1 % of each other (24 / 19: the
-// last CTA 3.5 % after the median).
-constexpr uint32_t kCostSymFar = 18, kCostSymNear = 36, kCostDiagFar = 13, kCostDiagNear = 28;
+// Relative cost of a stream-K unit (KBP j-sets of an item, at whose end
+// the CTA's warps meet at a barrier): the slowest warp's FP32-pipe cycles
+// per lane and step over the unit's j-sets -- far pairs 18 off the diagonal
+// (13 on it: i-side only), near pairs 24 (19) -- plus 28 that every unit
+// costs alike.  That constant was fitted to per-CTA timers: with 1 the CTAs'
+// times grew with their number of units (regression slope ~40 % of a
+// unit's mean time); with 28 the last CTA of a 2^20 Plummer evaluation ends
+// 0.2 % after the mean (0.9 % with the earlier per-item sum of all warps'
+// j-sets), of a 2^18 one 1.1 %.  The FP64 kernel's units all cost the same.
+constexpr uint32_t kCostSymFar = 18, kCostSymNear = 24, kCostDiagFar = 13, kCostDiagNear = 19;
+constexpr uint32_t kCostSymUnit = 28;
 
 __device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64_t &J) {
     const double b = 2.0 * (double)nb + 1.0;
@@ -606,7 +610,35 @@ __device__ __forceinline__ void item_of(int64_t t, int64_t nb, int64_t &I, int64
     J = r + (t - row_start(r, nb));
 }
 
-// One warp per item: the near/far decisions the pair kernel will take.
+// The adaptive FP32 kernel's unit costs of item t, one thread: the same
+// sums as sym_cost_kernel<2, NW, JSP> (which adds them up per item).
+__device__ void item_unit_costs(const SymParams &p, int64_t t, uint32_t (&uc)[US]) {
+    int64_t I, J;
+    item_of(t, p.nb, I, J);
+    const bool sym = I != J;
+    const uint32_t cn = sym ? kCostSymNear : kCostDiagNear;
+    const uint32_t cf = sym ? kCostSymFar : kCostDiagFar;
+    for (int u = 0; u < US; ++u) uc[u] = 0;
+    for (int w = 0; w < NW; ++w) {
+        float wb[7];
+        for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + (I * NW + w) * 8 + a);
+        for (int u = 0; u < US; ++u) {
+            uint32_t sum = 0;
+            for (int k = 0; k < KBP; ++k) {
+                float tb[7];
+                for (int a = 0; a < 7; ++a) tb[a] = __ldg(p.jbox + (J * NJSP + u * KBP + k) * 8 + a);
+                sum += boxes_near(wb, tb, p.gamma) ? cn : cf;
+            }
+            uc[u] = sum > uc[u] ? sum : uc[u];
+        }
+    }
+    for (int u = 0; u < US; ++u) uc[u] += kCostSymUnit;
+}
+
+// One warp per item: the near/far decisions the pair kernel will take.  For
+// the adaptive FP32 kernel lane l takes j-set l (unit l / 2): the unit's
+// cost is the maximum over the warps of its two j-sets' sum; other modes
+// give every unit the same cost.
 template <int MODE, int NWK, int JSET>
 __global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32_t *cost) {
     constexpr int NJ = BI / JSET;  // j-sets per block
@@ -620,23 +652,24 @@ __global__ void __launch_bounds__(256) sym_cost_kernel(const SymParams p, uint32
     const uint32_t cn = sym ? kCostSymNear : kCostDiagNear;
     const uint32_t cf = sym ? kCostSymFar : kCostDiagFar;
     uint32_t c = 0;
-    if (MODE != 2) {
-        c = (MODE == 1 ? cn : cf) * (NJ / 32) * NWK;  // this lane's j-sets x the block's warps
+    if constexpr (MODE != 2) {
+        // every unit of the item alike (every j-set near for MODE 1)
+        c = (l & 1) ? 0u : 2 * (MODE == 1 ? cn : cf) + kCostSymUnit;
     } else {
-        constexpr int H = NJ / 32;  // j-sets of the block per lane
-        float tb[H][7];
+        static_assert(NJ == 32 && KBP == 2 && NWK == NW, "lane l: j-set l, unit l / 2");
+        float tb[7];
 #pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-            for (int a = 0; a < 7; ++a)
-                tb[h][a] = __ldg(p.jbox + (J * BI / JSET + l + 32 * h) * 8 + a);
+        for (int a = 0; a < 7; ++a) tb[a] = __ldg(p.jbox + (J * NJ + l) * 8 + a);
+        uint32_t m = 0;
         for (int w = 0; w < NWK; ++w) {
             float wb[7];
 #pragma unroll
             for (int a = 0; a < 7; ++a) wb[a] = __ldg(p.wbox + ((I * BI + w * WS) / WS) * 8 + a);
-#pragma unroll
-            for (int h = 0; h < H; ++h) c += boxes_near(wb, tb[h], p.gamma) ? cn : cf;
+            const uint32_t v = boxes_near(wb, tb, p.gamma) ? cn : cf;
+            const uint32_t pair = v + __shfl_xor_sync(0xffffffffu, v, 1);
+            m = pair > m ? pair : m;
         }
+        c = (l & 1) ? 0u : m + kCostSymUnit;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -672,9 +705,13 @@ __global__ void __launch_bounds__(1024) sym_scan_kernel(const uint32_t *cost, in
 }
 
 // lo[c] = the unit where the cumulative cost reaches c / ctas of the total
-// (linear inside an item); lo[0] = 0, lo[ctas] = U, non-decreasing.
-__global__ void sym_ranges_kernel(const uint32_t *cost, const unsigned long long *prefix,
-                                  int64_t T, int64_t ctas, int64_t *lo) {
+// (the nearest unit boundary, from the item's unit costs for the adaptive
+// kernel, linearly inside an item otherwise); lo[0] = 0, lo[ctas] = U,
+// non-decreasing.
+template <int MODE>
+__global__ void sym_ranges_kernel(const SymParams p, const uint32_t *cost,
+                                  const unsigned long long *prefix, int64_t T, int64_t ctas,
+                                  int64_t *lo) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ctas;
          c += (int64_t)gridDim.x * blockDim.x) {
         if (c == 0 || c == ctas) {
@@ -690,8 +727,19 @@ __global__ void sym_ranges_kernel(const uint32_t *cost, const unsigned long long
             else
                 b = m - 1;
         }
-        int64_t off = (int64_t)((target - prefix[a]) * (unsigned long long)US / cost[a]);
-        if (off > US) off = US;
+        const unsigned long long r = target - prefix[a];
+        int64_t off;
+        if (MODE == 2) {
+            uint32_t uc[US];
+            item_unit_costs(p, a, uc);
+            unsigned long long run = 0;
+            off = 0;
+            while (off < US && run + uc[off] <= r) run += uc[off++];
+            if (off < US && 2 * (r - run) > uc[off]) ++off;  // the nearer boundary
+        } else {
+            off = (int64_t)(r * (unsigned long long)US / cost[a]);
+            if (off > US) off = US;
+        }
         lo[c] = a * US + off;
     }
 }
@@ -716,13 +764,13 @@ int launch_pair(const SymParams &p, cudaStream_t st) {
 // (8 warps x 64-slot j-sets).
 template <int MODE, bool FP64 = false>
 int launch_split(const SymParams &p, const ForceJob &j, const SymLayout &y) {
-    if (FP64)
-        sym_cost_kernel<MODE, SW, JS><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
+    if constexpr (FP64)
+        sym_cost_kernel<0, SW, JS><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
     else
         sym_cost_kernel<MODE, NW, JSP><<<(unsigned)cdiv(p.T * 32, 256), 256, 0, j.stream>>>(p, y.cost);
     sym_scan_kernel<<<1, 1024, 0, j.stream>>>(y.cost, p.T, y.prefix);
-    sym_ranges_kernel<<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
-        y.cost, y.prefix, p.T, p.ctas, y.lo);
+    sym_ranges_kernel<FP64 ? 0 : MODE><<<(unsigned)cdiv(p.ctas + 1, 256), 256, 0, j.stream>>>(
+        p, y.cost, y.prefix, p.T, p.ctas, y.lo);
     sym_exponent_kernel<<<(unsigned)std::min<int64_t>(cdiv(j.N, 4 * 256), 1024), 256, 0,
                           j.stream>>>(j.mass, j.N, j.eps, y.fx_exp, y.mmax_bits, y.arrivals);
     count_launch(4);
