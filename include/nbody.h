@@ -173,12 +173,14 @@ const char *nb_last_error(void);
 
 /*
  * Self-check of the integer-pipe float <-> double conversions and
- * finiteness test that FP64-bound kernels use: on the host, the same
- * source's results for every float exponent with edge significands, every
- * double exponent with significands at the rounding boundaries, and 3 n
- * seeded random float patterns and 2 n double patterns (splitmix64 from
- * `seed`) are compared bit for bit with the C conversions (round to nearest
- * even) and isfinite;
+ * finiteness test that FP64-bound kernels use, and of the fixed-point split
+ * of FP64 partials: on the host, the same source's results for every float
+ * exponent with edge significands, every double exponent with significands
+ * at the rounding boundaries, 3 n seeded random float patterns and 2 n
+ * double patterns (splitmix64 from `seed`), and edge and n random
+ * (value, exponent) pairs for the split, are compared with the C
+ * conversions (round to nearest even), isfinite and v 2^F rounded half away
+ * from zero;
  * *mismatches receives the count (0 when they agree).  No device work.
  * NB_ERR_INVALID for a NULL pointer or n < 0.
  */

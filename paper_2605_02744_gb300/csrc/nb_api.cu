@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "nb_fixed.cuh"
 #include "nb_fpconv.cuh"
 #include "nb_internal.h"
 
@@ -452,6 +453,39 @@ int nb_check_fp_conversions(int64_t n, uint64_t seed, int64_t *mismatches) {
         const uint64_t m = (r & 0xfffffe0000000ull) |
                            (t == 0 ? 0x10000000ull : t == 1 ? 0x0fffffffull : (r & 0x1fffffffull));
         check_d((r & 0x8000000000000000ull) | (e << 52) | m);
+    }
+    // the fixed-point split of FP64 partials: hi 2^40 + lo (two's
+    // complement) is v 2^F rounded half away from zero, or nothing past 2^100
+    auto check_split = [&](double v, int F) {
+        unsigned long long hi, lo;
+        const bool ok = fx::split_f64(v, F, hi, lo);
+        const double X = std::ldexp(v, F);  // exact: a power-of-two scaling
+        if (!std::isfinite(v) || !(std::fabs(X) < 0x1p100)) {
+            if (ok && std::isfinite(v) && std::fabs(X) < 0x1p100) ++bad;
+            if (!std::isfinite(v) && ok) ++bad;
+            return;
+        }
+        if (!ok) { ++bad; return; }
+        const double ax = std::fabs(X);
+        unsigned __int128 ref;
+        if (ax >= 0x1p52)
+            ref = (unsigned __int128)ax;            // already an integer
+        else
+            ref = (unsigned __int128)std::floor(ax + 0.5);  // exact below 2^52
+        const __int128 got = (__int128)(long long)hi * ((__int128)1 << fx::kLoBits) + (__int128)lo;
+        const __int128 want = std::signbit(v) ? -(__int128)ref : (__int128)ref;
+        if (got != want) ++bad;
+    };
+    for (int F : {-900, -60, -1, 0, 1, 40, 60, 99, 120, 900})
+        for (double v : {0.0, -0.0, 1.0, -1.0, 0.5, -0.5, 1.5, 2.5, -2.5, 0x1p-1074, 1e300, -1e-300,
+                         0x1p99, 0x1.fffffffffffffp99, 0x1p100, 3.0 * 0x1p-60, 0x1p-61})
+            check_split(v, F);
+    for (int64_t k = 0; k < n; ++k) {
+        const uint64_t r = next();
+        const int F = (int)(next() % 301) - 150;
+        // magnitudes around the grid and the bound of that F
+        const uint64_t e = (uint64_t)(1023 - F - 60 + (int)((r >> 56) % 170));
+        check_split(fpconv::from_bits_d((r & 0x800fffffffffffffull) | ((e & 0x7ff) << 52)), F);
     }
     *mismatches = bad;
     return NB_OK;

@@ -2,7 +2,8 @@
 // two-word fixed point, for sums that many CTAs add to at once.
 //
 // A call fixes one exponent F for every accumulator.  A partial sum v (FP32
-// or FP64) becomes the integer X = rint(v 2^F), split as X = hi 2^40 + lo
+// or FP64) becomes the integer X = v 2^F rounded half away from zero (in
+// integer arithmetic on the bits of v), split as X = hi 2^40 + lo
 // with 0 <= lo < 2^40; hi goes into one 64-bit word and lo into another with
 // integer atomic adds.  Integer addition is associative, so the words end the
 // same whatever order the adds arrive in: results are bitwise reproducible,
@@ -15,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "nb_internal.h"
 
@@ -34,17 +36,53 @@ __host__ __device__ inline int exponent_for(double bound) {
     return F < -900 ? -900 : (F > 900 ? 900 : F);
 }
 
+// The two words' increments (hi, lo) of an FP64 partial v, in integer
+// arithmetic on its bits (no FP64 operations, which are slow on this part):
+// with v = m 2^(k - 52), m the 53-bit significand, X = m 2^(k - 52 + F) is m
+// shifted left (exact) or right (rounded half away from zero), split as
+// |X| = H 2^40 + L and negated in two's complement for v < 0.  false (no
+// increments) if v is not finite or |X| >= 2^100.  The same source runs on
+// the host, where nb_check_fp_conversions checks it.
+__host__ __device__ inline bool split_f64(double v, int F, unsigned long long &hi,
+                                          unsigned long long &lo) {
+    unsigned long long b;
+    memcpy(&b, &v, 8);
+    const int be = (int)((b >> 52) & 0x7ffu);
+    hi = lo = 0;
+    if (be == 0x7ff) return false;  // inf or NaN
+    unsigned long long m = b & 0xfffffffffffffull;
+    if (be) m |= 1ull << 52;
+    if (!m) return true;  // +-0
+    const int s = (be ? be : 1) - 1075 + F;  // X = m 2^s
+    unsigned __int128 X;
+    if (s >= 0) {
+        if (s > kMagBits - 53) return false;  // beyond the bound
+        X = (unsigned __int128)m << s;
+    } else {
+        if (s < -54) return true;  // below half a grid step
+        X = ((unsigned __int128)m + ((unsigned __int128)1 << (-s - 1))) >> (-s);
+    }
+    if (X >> kMagBits) return false;
+    const unsigned long long H = (unsigned long long)(X >> kLoBits);
+    const unsigned long long L = (unsigned long long)X & ((1ull << kLoBits) - 1);
+    if (b >> 63) {  // two's complement of H 2^40 + L
+        hi = L ? ~H : (0ull - H);
+        lo = L ? (1ull << kLoBits) - L : 0ull;
+    } else {
+        hi = H;
+        lo = L;
+    }
+    return true;
+}
+
 // Adds v to accumulator (word_hi, word_lo); false (nothing added) if v is
 // not finite or outside the bound.
 __device__ __forceinline__ bool add(unsigned long long *word_hi, unsigned long long *word_lo,
                                     double v, int F) {
-    const double X = rint(ldexp(v, F));
-    if (!(fabs(X) < 0x1p100)) return false;  // NaN, inf, or beyond the bound
-    const double h = floor(X * 0x1p-40);
-    const long long hi = (long long)h;
-    const unsigned long long lo = (unsigned long long)(X - h * 0x1p40);
-    if (hi != 0) atomicAdd(word_hi, (unsigned long long)hi);
-    if (lo != 0) atomicAdd(word_lo, lo);
+    unsigned long long hi, lo;
+    if (!split_f64(v, F, hi, lo)) return false;
+    if (hi) atomicAdd(word_hi, hi);
+    if (lo) atomicAdd(word_lo, lo);
     return true;
 }
 
