@@ -135,6 +135,18 @@ def test_step_and_vjp_argument_checks(B):
                            ctypes.byref(o)) == 1
     assert lib.nb_step_vjp(FAKE, FAKE, 16, 0.1, 1e-3, 5e-4, FAKE, None, FAKE, FAKE, wsb,
                            ctypes.byref(o)) == 1
+    # row ranges: a bad range, a non-finite coefficient, a missing cotangent
+    for i0, i1 in ((-1, 4), (4, 4), (0, 17)):
+        assert lib.nb_forces_range(FAKE, FAKE, 16, i0, i1, 0.1, FAKE, None, FAKE, wsb,
+                                   ctypes.byref(o)) == 1
+        assert lib.nb_forces_vjp_range(FAKE, FAKE, 16, i0, i1, 0.1, 1.0, FAKE, None, FAKE, FAKE,
+                                       FAKE, wsb, ctypes.byref(o)) == 1
+    assert lib.nb_forces_vjp_range(FAKE, FAKE, 16, 0, 8, 0.1, float("nan"), FAKE, None, FAKE,
+                                   FAKE, FAKE, wsb, ctypes.byref(o)) == 1
+    assert lib.nb_forces_vjp_range(FAKE, FAKE, 16, 0, 8, 0.1, 1.0, None, None, FAKE, FAKE, FAKE,
+                                   wsb, ctypes.byref(o)) == 1
+    assert lib.nb_kick_drift(FAKE, FAKE, FAKE, 0, 0.5, 1.0, ctypes.byref(o)) == 1
+    assert lib.nb_kick_drift(FAKE, FAKE, FAKE, 4, float("inf"), 1.0, ctypes.byref(o)) == 1
     assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 0, 16, FAKE, FAKE, None, FAKE, 1 << 30,
                                  ctypes.byref(o)) == 1
     assert lib.nb_forces_batched(FAKE, FAKE, FAKE, 4, 3, FAKE, FAKE, None, FAKE, 1 << 30,
