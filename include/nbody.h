@@ -105,8 +105,9 @@ typedef enum {
  * For batches (B > 1, nb_forces_batched and
  * nb_step with offsets) DEFAULT and SYMMETRIC take the symmetric batched
  * path (warp-granular work items; workspace about 250 B per particle plus
- * 2 KiB per pair of 128-particle blocks of a cluster: 0.9 GB for 512
- * clusters of up to 8192) and DIRECT the persistent direct-pair kernel
+ * 2 KiB per pair of 128-particle blocks of a cluster, provisioned for 64
+ * such pairs per block: 1.4 GB for the 512 clusters of 64 to 8192) and
+ * DIRECT the persistent direct-pair kernel
  * (nb_tune's cluster_ctas / threads).  Results of both are deterministic;
  * they differ from each other by summation order only. */
 typedef enum {
